@@ -1,0 +1,449 @@
+"""Benchmark: batched SALT chi^2 + gradient on one B300 (per rank).
+
+One step = one salt_chi2_grad call over the whole batch (phase/wavelength,
+bicubic M0/M1, colour law, band integral, zero point, FP64 chi^2 and the
+adjoint gradient) through the fused persistent factorised kernel. The primary
+workload is the 1000-supernova batched configuration (6 bands, 20-200
+observations, one parameter vector each); inputs are resident in HBM and L2 is
+flushed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own seeded batch of the same shape (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "bandfluxes/s and chi2+grad evals/s on 1 B300 vs oracle; serving p50/p99 ms"
+UNIT = "bandfluxes/s"
+
+# Algorithmic FP32 work of the factorised method (FLOP per unit; each FMA = 2).
+FLOP_K_GRAD = 74     # per (sample, band, in-grid band sample): lambda', Keys weights and
+                     # derivatives, colour law + slope, exp2, 12 weighted taps, 12 gather adds
+FLOP_K_FWD = 33
+FLOP_RC_GRAD = 8     # per (sample, band, touched row, window column): forward + reverse FMA pair
+FLOP_RC_FWD = 4
+FLOP_C_GRAD = 4      # per (sample, band, window column): Q . E_c, Q . E_z
+FLOP_OBS_GRAD = 60   # per (sample, observation): phase taps, 4-row combine, residual, gradient
+FLOP_OBS_FWD = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5])
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle CPU-baseline budget")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_workload(config: int, rank: int):
+    seed = 1000 + config + 7919 * rank
+    wl = W.make(config, seed=seed)
+    W.template_flux(wl.batch, np.random.default_rng(seed + 1))
+    return wl
+
+
+def algorithmic_flops(wl, grad=True, max_par=2_000_000):
+    """Exact count of the factorised method's necessary FP32 work for one
+    pass over the batch: per (sample, band) the in-grid band samples, the
+    window columns and the distinct phase rows its own observations touch."""
+    m, bt = wl.model, wl.batch
+    nb = len(wl.bands)
+    lam_lo = np.array([b.wave[0] for b in wl.bands])
+    lam_hi = np.array([b.wave[-1] for b in wl.bands])
+    waves = [np.asarray(b.wave, dtype=np.float64) for b in wl.bands]
+    n_obs = np.diff(bt.obs_off)
+    n_par = np.diff(bt.par_off)
+    total = 0.0
+    rng = np.random.default_rng(0)
+    # subsample very large batches and scale (the count is a sum over samples)
+    idx_all = np.arange(bt.n_par)
+    scale = 1.0
+    if bt.n_par > max_par:
+        idx_all = np.sort(rng.choice(bt.n_par, max_par, replace=False))
+        scale = bt.n_par / max_par
+    sn_of = np.repeat(np.arange(bt.n_sn), n_par)
+    for chunk in np.array_split(idx_all, max(1, len(idx_all) // 20000)):
+        for j in chunk:
+            s = sn_of[j]
+            lo, hi = bt.obs_off[s], bt.obs_off[s + 1]
+            if hi == lo:
+                continue
+            a = 1.0 / (1.0 + float(bt.z[j]))
+            p = (bt.mjd[lo:hi] - bt.t0[j]) * a
+            bands = bt.band[lo:hi]
+            ok = (p >= m.phase0) & (p <= m.phase_max)
+            iv = np.clip(np.floor((p - m.phase0) / m.dphase).astype(np.int64), 0, m.n_phase - 2)
+            first = np.where(iv == 0, 0, np.where(iv == m.n_phase - 2, m.n_phase - 4, iv - 1))
+            for b in np.unique(bands):
+                sel = (bands == b)
+                nb_obs = int(sel.sum())
+                fr = first[sel & ok]
+                rows = np.unique((fr[:, None] + np.arange(4)[None, :]).ravel()).size if fr.size else 0
+                lr = waves[b] * a
+                kin = int(((lr >= m.wave0) & (lr <= m.wave_max)).sum())
+                if kin:
+                    lri = lr[(lr >= m.wave0) & (lr <= m.wave_max)]
+                    c0 = np.clip(np.floor((lri[[0, -1]] - m.wave0) / m.dwave).astype(np.int64), 0,
+                                 m.n_wave - 2)
+                    f0 = [0 if c == 0 else (m.n_wave - 4 if c == m.n_wave - 2 else c - 1) for c in c0]
+                    cols = f0[1] + 3 - f0[0] + 1
+                else:
+                    cols = 0
+                if grad:
+                    total += (FLOP_K_GRAD * kin + FLOP_RC_GRAD * rows * cols + FLOP_C_GRAD * cols
+                              + FLOP_OBS_GRAD * nb_obs)
+                else:
+                    total += FLOP_K_FWD * kin + FLOP_RC_FWD * rows * cols + FLOP_OBS_FWD * nb_obs
+    del lam_lo, lam_hi, nb
+    return total * scale
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason sampling during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        time.sleep(0.25)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the same workload per step."""
+    if rank != 0:
+        return
+    import oracle
+    wl = make_workload(args.workload, 0)
+    bt = wl.batch
+    o = oracle.Oracle(wl.model, wl.bands)
+    # per step: the first supernovae of the batch up to ~1/4 s of CPU work
+    n_sn = min(bt.n_sn, 250 if args.workload == 2 else 8)
+    sub = W.subset(bt, np.arange(n_sn))
+    for _ in range(args.warmup):
+        o.chi2(sub, grad=True)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.chi2(sub, grad=True)
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(t)
+    nbf = sub.n_bandflux()
+    value = nbf / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W.CONFIG_NAMES[args.workload], "sample_supernovae": n_sn},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+                         "sample": f"first {n_sn} supernovae ({nbf} bandfluxes) per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def time_steps(fn, steps, warmup, stream, flush=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    durs = []
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        durs.append(e0.elapsed_time(e1))
+    return durs
+
+
+def secondary(args, salt_mod, torch, dev, stream):
+    """Shorter measurements of the other workloads (not the bench line)."""
+    from paper_2504_08081_b300.torch_api import Salt
+    out = {}
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for cfg in (3, 5):
+        wl = make_workload(cfg, 0)
+        s = Salt(wl.model, wl.bands, device=dev.index or 0)
+        with torch.cuda.stream(stream):
+            db = s.upload(wl.batch)
+            torch.cuda.synchronize()
+            durs = time_steps(lambda: s.chi2_grad(db), 5, 2, stream, flush=flush_buf.zero_)
+        ms = statistics.median(durs)
+        nbf = wl.batch.n_bandflux()
+        flops = algorithmic_flops(wl, grad=True, max_par=20000)
+        out[W.CONFIG_NAMES[cfg]] = {"ms_per_step": ms, "bandfluxes_per_s": nbf / (ms / 1e3),
+                                    "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3),
+                                    "bandfluxes": nbf, "samples": wl.batch.n_par,
+                                    "achieved_tflops": flops / (ms / 1e3) / 1e12}
+        s.close()
+        del db
+    try:
+        from workloads import serving as SV
+        out[W.CONFIG_NAMES[4]] = SV.run_serving_bench(dev.index or 0)
+    except ImportError:
+        pass
+    return out
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2504_08081_b300 import build as B
+    B.build()
+    from paper_2504_08081_b300.torch_api import Salt
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = make_workload(args.workload, rank)
+    bt = wl.batch
+    stream = torch.cuda.Stream(dev)
+    salt = Salt(wl.model, wl.bands, device=local_rank)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    with torch.cuda.stream(stream):
+        db = salt.upload(bt)
+        chi2 = torch.empty(bt.n_par, dtype=torch.float64, device=dev)
+        grad = torch.empty((bt.n_par, 5), dtype=torch.float32, device=dev)
+        step = lambda: salt.chi2_grad(db, chi2, grad)  # noqa: E731
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            t_wall = time.perf_counter()
+            durs = time_steps(step, args.steps, 0, stream, flush=flush_buf.zero_)
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter() - t_wall
+        barrier()
+        salt.check()
+    ms = statistics.mean(durs)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    nbf_t = torch.tensor([float(bt.n_bandflux()), float(bt.n_par)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(nbf_t, op=dist.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    n_bf_all, n_par_all = float(nbf_t[0].item()), float(nbf_t[1].item())
+    value = n_bf_all / (ms_max / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs -> device -> host results
+    obs_names = ["mjd", "band", "flux", "fluxerr", "zp"]
+    par_names = ["t0", "z", "x0", "x1", "c"]
+    host = {k: db.t[k].cpu().pin_memory() for k in obs_names + par_names}
+    chi2_h = torch.empty(bt.n_par, dtype=torch.float64).pin_memory()
+    grad_h = torch.empty((bt.n_par, 5), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = chi2_h.numel() * 8 + grad_h.numel() * 4
+    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    from paper_2504_08081_b300.torch_api import DeviceBatch
+    db2 = DeviceBatch(db.obs_off, db.par_off, dev_in, db.plan)
+
+    def e2e_step():
+        for k in host:
+            dev_in[k].copy_(host[k], non_blocking=True)
+        salt.chi2_grad(db2, chi2, grad)
+        chi2_h.copy_(chi2, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_durs = time_steps(e2e_step, args.steps, max(args.warmup, 3), stream, flush=flush_buf.zero_)
+    e2e_ms = statistics.mean(e2e_durs)
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = n_bf_all / (float(e2e_t.item()) / 1e3)
+    np.testing.assert_array_equal(chi2_h.numpy(), chi2.cpu().numpy())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (fused factorised chi^2+grad)
+    flops = algorithmic_flops(wl, grad=True)
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    max_mhz = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
+    fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the max SM clock
+    achieved = flops / (ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "salt::fk::k_fact<8,MODE_GRAD>" if db.plan is None else
+                          f"salt::fk::k_fact<{salt_tile(db)},MODE_GRAD>",
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "flop_per_launch": flops}
+
+    # ---- CPU baseline: the oracle as it stands, on the host cores
+    cpu = cpu_baseline(wl, args.cpu_seconds)
+
+    extras = {}
+    if world == 1 and not args.no_extras:
+        try:
+            extras = secondary(args, None, torch, dev, stream)
+        except Exception as ex:  # secondary numbers must not sink the bench line
+            extras = {"error": repr(ex)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 epoch difference and chi2 sum)",
+        "data": "synthetic (seeded; model-free template fluxes)",
+        "config": {"workload": W.CONFIG_NAMES[args.workload], "supernovae": bt.n_sn * world,
+                   "bandfluxes_per_step": int(n_bf_all), "samples_per_step": int(n_par_all),
+                   "bands": len(wl.bands), "grid": [wl.model.n_phase, wl.model.n_wave],
+                   "step": "salt_chi2_grad (chi2 + adjoint gradient)",
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "chi2_grad_evals_per_s": n_par_all / (ms_max / 1e3),
+        "gpu_launches": args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+        "secondary": extras,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def salt_tile(db):
+    tot = db.n_par / max(db.n_sn, 1)
+    return 8 if tot >= 8 else 4 if tot >= 4 else 2 if tot >= 2 else 1
+
+
+def cpu_baseline(wl, budget_s):
+    import oracle
+    o = oracle.Oracle(wl.model, wl.bands)
+    bt = wl.batch
+    done, n_bf, t = 0, 0, 0.0
+    # whole batch passes until the budget is spent (at least one)
+    while True:
+        t0 = time.perf_counter()
+        o.chi2(bt, grad=True)
+        t += time.perf_counter() - t0
+        done += 1
+        n_bf += bt.n_bandflux()
+        if t >= budget_s or done >= 50:
+            break
+    return {"value": n_bf / t, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+            "sample": f"{done} full pass(es) of the {bt.n_sn}-supernova batch, chi2+grad, "
+                      f"FP64 C with OpenMP ({t:.1f} s)"}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

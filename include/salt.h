@@ -1,0 +1,234 @@
+/*
+ * salt.h - C ABI of the B300 (sm_103a) batched SALT synthetic-photometry library.
+ *
+ * What is computed (JAX-bandflux, arXiv:2504.08081, Implementation section):
+ *   SALT model form, Eq. 1:
+ *       F(p, lambda) = x0 [M0(p, lambda) + x1 M1(p, lambda)] * 10^(-0.4 c CL(lambda))
+ *     (the paper's exp[c CL] with its CL = -0.4 ln10 times this CL), where the
+ *     free parameters are x0, x1, t0 and c; p = (t - t0)/(1 + z) is the
+ *     rest-frame phase and lambda = lambda_obs/(1 + z) the rest wavelength; the
+ *     observer-frame flux density is F/(1 + z).
+ *   Bandflux, Eq. 2:  integral F(lambda) T(lambda) lambda/(h c) dlambda, taken
+ *     with the trapezoidal rule on the band's own samples (paragraph after
+ *     Eq. 2), scaled to the observation's AB zero point by 10^(0.4 zp) / Z_b
+ *     where Z_b is the same integral of the 3631 Jy AB spectrum.
+ *   chi^2 = sum_i ((flux_i - bandflux_i) / fluxerr_i)^2 per parameter sample,
+ *     and its gradient with respect to (z, t0, x0, x1, c) (the paper's claim
+ *     of gradient propagation through the whole pipeline, Implementation,
+ *     last paragraph).
+ *   M0/M1 are interpolated with tensor-product Keys cubic convolution
+ *   (a = -1/2; linear on the first and last interval of each axis; zero
+ *   outside the grid): the paper's "dedicated interpolation routines". The
+ *   colour law is the SALT2 polynomial with linear extrapolation outside
+ *   [cl_lo, cl_hi].
+ *
+ * Conventions for every call:
+ *   - Status codes are returned; no C++ exception crosses this boundary. The
+ *     text of the last error on a context is available from salt_last_error.
+ *   - Batch calls are asynchronous on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - The caller owns every batch array and every output buffer. The library
+ *     owns everything reachable from a salt_ctx or a salt_plan.
+ *   - Precision: FP32 arithmetic, except the epoch difference t - t0 (FP64,
+ *     MJD values) and the chi^2 accumulation (FP64).
+ *   - Thread safety: batch calls on one context from one thread at a time;
+ *     salt_serve_* calls are safe from any thread.
+ */
+#ifndef SALT_H
+#define SALT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SALT_ABI_VERSION 1
+#define SALT_MAX_BANDS 64
+
+typedef enum {
+    SALT_OK = 0,
+    SALT_PENDING = 1,          /* serving: request not finished yet */
+    SALT_ERR_INVALID = -1,     /* argument or data failed validation */
+    SALT_ERR_OOM = -2,         /* device or host allocation failed, or can never fit */
+    SALT_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    SALT_ERR_TIMEOUT = -4,     /* serving: wait_ms elapsed */
+    SALT_ERR_NOT_FOUND = -5,   /* serving: unknown or already collected ticket */
+    SALT_ERR_CANCELLED = -6,   /* serving: request was cancelled */
+    SALT_ERR_DATA = -7         /* a kernel met invalid batch data (see salt_check) */
+} salt_status;
+
+typedef struct salt_ctx salt_ctx;
+typedef struct salt_plan salt_plan;
+
+/* ---------------------------------------------------------------- model --- */
+
+/* Model grid (Eq. 1 surfaces) on uniform axes. HOST pointers, copied.
+ *   phase axis: phase0 + r*dphase, r < n_phase (days); wave axis: wave0 +
+ *   j*dwave, j < n_wave (Angstrom). n_phase, n_wave >= 4.
+ *   m0, m1: row-major [n_phase][n_wave] float32.
+ *   cl: n_cl == 4 colour-law coefficients a1..a4 of
+ *       P(x) = (1 - sum a) x + a1 x^2 + a2 x^3 + a3 x^4 + a4 x^5,
+ *       x = (lambda - 4302.57)/(5428.55 - 4302.57), CL = -P on [cl_lo, cl_hi],
+ *       linear continuation outside. */
+typedef struct {
+    int32_t n_phase, n_wave;
+    double phase0, dphase, wave0, dwave;
+    const float *m0, *m1;
+    int32_t n_cl;
+    const double *cl;
+    double cl_lo, cl_hi;
+} salt_model_desc;
+
+/* A bandpass (paper: Bandpass / register_bandpass): n >= 2 samples of
+ * strictly ascending wavelength (Angstrom) and transmission. HOST, copied. */
+typedef struct {
+    int32_t n;
+    const double *wave, *trans;
+} salt_band_desc;
+
+/* Create a context on CUDA device `device`: uploads the grids, registers the
+ * bands (band id = index in `bands`, n_bands <= SALT_MAX_BANDS), precomputes
+ * the trapezoid weights lambda T Delta/(h c Z_b) in FP64 on the host and
+ * rounds them to float32. serve_mem_bytes bounds the device memory the serving
+ * engine may hold for admitted requests (0 = no serving engine).
+ * Returns SALT_ERR_INVALID for a non-finite grid, axes with n < 4 or a
+ * non-positive step, bands with n < 2 or non-ascending wavelengths;
+ * SALT_ERR_CUDA / SALT_ERR_OOM on device failures. *out is NULL on error. */
+int salt_init_model(const salt_model_desc *model, const salt_band_desc *bands, int32_t n_bands,
+                    int32_t device, size_t serve_mem_bytes, salt_ctx **out);
+
+/* Stop the serving engine (pending requests are cancelled), free everything. */
+void salt_destroy(salt_ctx *ctx);
+
+/* ---------------------------------------------------------------- batches - */
+
+/* A ragged batch (the paper's vmap over data instances, Implementation,
+ * paragraph after Eq. 2). Supernova s owns observations [obs_off[s],
+ * obs_off[s+1]) and parameter samples [par_off[s], par_off[s+1]).
+ *   obs_off, par_off: HOST int64 [n_sn + 1], nondecreasing, starting at 0.
+ *   mjd[n_obs] (FP64), band[n_obs] (band id), flux, fluxerr (> 0), zp (AB):
+ *     DEVICE arrays.
+ *   t0[n_par] (FP64, MJD), z (> -1), x0, x1, c [n_par]: DEVICE arrays.
+ *   plan: optional, from salt_plan_create with the same offsets (saves the
+ *     host-side planning and the offset upload on every call); NULL = plan
+ *     on the fly.
+ *   validate: nonzero = check band ids, fluxerr > 0 and finite parameters on
+ *     the device first and return SALT_ERR_INVALID (outputs untouched) if any
+ *     fails; this synchronises the stream. With validate = 0 the kernels still
+ *     never read out of bounds: an observation with a bad band id or
+ *     fluxerr <= 0 makes its sample's outputs NaN and records SALT_ERR_DATA,
+ *     reported by salt_check. */
+typedef struct {
+    int64_t n_sn;
+    const int64_t *obs_off;
+    const int64_t *par_off;
+    const double *mjd;
+    const int32_t *band;
+    const float *flux, *fluxerr, *zp;
+    const double *t0;
+    const float *z, *x0, *x1, *c;
+    const salt_plan *plan;
+    int32_t validate;
+} salt_batch;
+
+/* Precompute the launch plan for a batch layout (host CSR offsets): the
+ * cost-sorted work list of (supernova, sample-tile) items, the device copies
+ * of the offsets and the tile choice. Reusable for every batch with the same
+ * offsets (the parameters and observation values may change between calls). */
+int salt_plan_create(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,
+                     salt_plan **out);
+void salt_plan_destroy(salt_plan *plan);
+
+/* Offsets of the bandflux output: bf_off[s] = sum_{s'<s} n_obs(s') n_par(s'),
+ * bf_off[n_sn] = total. HOST in, HOST out ([n_sn + 1]). */
+int salt_bandflux_offsets(int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,
+                          int64_t *bf_off);
+
+/* Bandflux (Eq. 2, zero-point scaled) of every (sample, observation) pair of
+ * every supernova: out[bf_off[s] + j*n_obs(s) + i] for local sample j and
+ * local observation i. out: DEVICE float32 [bf_off[n_sn]]. */
+int salt_bandflux(salt_ctx *ctx, const salt_batch *batch, float *out, void *cuda_stream);
+
+/* chi^2 of every parameter sample against its supernova's observations.
+ * chi2: DEVICE float64 [n_par]. */
+int salt_chi2(salt_ctx *ctx, const salt_batch *batch, double *chi2, void *cuda_stream);
+
+/* chi^2 and its gradient d chi^2 / d(z, t0, x0, x1, c) (hand-written adjoint).
+ * chi2: DEVICE float64 [n_par]; grad: DEVICE float32 [n_par][5]. */
+int salt_chi2_grad(salt_ctx *ctx, const salt_batch *batch, double *chi2, float *grad,
+                   void *cuda_stream);
+
+/* Synchronise `cuda_stream` and report SALT_ERR_DATA if any kernel since the
+ * last salt_check met invalid batch data (the sticky flag is then cleared),
+ * SALT_ERR_CUDA on an asynchronous CUDA error, else SALT_OK. */
+int salt_check(salt_ctx *ctx, void *cuda_stream);
+
+/* ---------------------------------------------------------------- options - */
+
+typedef enum {
+    SALT_OPT_KERNEL = 1,       /* SALT_KERNEL_* : which kernel family batch calls use */
+    SALT_OPT_TILE_SAMPLES = 2, /* samples per work item (0 = autotuned / default) */
+    SALT_OPT_GRAPHS = 3,       /* 1 = replay batch calls from captured CUDA graphs (default 1) */
+    SALT_OPT_SERVE_CHUNK = 4   /* serving: samples per chunk (default 64) */
+} salt_option;
+
+typedef enum {
+    SALT_KERNEL_AUTO = 0,        /* factorised fused kernel */
+    SALT_KERNEL_DIRECT = 1,      /* per-band-sample evaluation straight from Eq. 1-2 */
+    SALT_KERNEL_FACTORISED = 2   /* per-(sample, band) column response, shared by observations */
+} salt_kernel;
+
+int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value);
+int salt_get_option(const salt_ctx *ctx, int32_t option, int64_t *value);
+
+/* ---------------------------------------------------------------- serving - */
+
+/* One serving request: one supernova, its observations and n_par parameter
+ * samples. HOST pointers; the library copies them at submit. */
+typedef struct {
+    int32_t n_obs, n_par, want_grad;
+    const double *mjd;
+    const int32_t *band;
+    const float *flux, *fluxerr, *zp;
+    const double *t0;
+    const float *z, *x0, *x1, *c;
+} salt_request;
+
+/* Queue a request for continuous batching. Returns SALT_ERR_INVALID for bad
+ * data (validated on the host), SALT_ERR_OOM if it can never fit in the
+ * serving memory budget. *ticket identifies it for poll/cancel. */
+int salt_serve_submit(salt_ctx *ctx, const salt_request *req, uint64_t *ticket);
+
+/* Wait up to wait_ms (0 = do not wait, < 0 = forever) for a request.
+ * SALT_OK: results copied to chi2 (HOST float64 [n_par]) and, if requested,
+ * grad (HOST float32 [n_par][5]); the ticket is then released.
+ * SALT_PENDING / SALT_ERR_TIMEOUT: not finished. SALT_ERR_CANCELLED,
+ * SALT_ERR_NOT_FOUND, SALT_ERR_CUDA otherwise. */
+int salt_serve_poll(salt_ctx *ctx, uint64_t ticket, int32_t wait_ms, double *chi2, float *grad);
+
+/* Cancel a queued or running request; its memory is released when any
+ * in-flight work on it completes. */
+int salt_serve_cancel(salt_ctx *ctx, uint64_t ticket);
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, rejected;
+    uint64_t launches;            /* fused kernel launches issued by the engine */
+    uint64_t queued, active;      /* current queue depth and admitted requests */
+    size_t mem_in_use, mem_limit; /* admitted device bytes and the budget */
+    double p50_ms, p99_ms;        /* submit -> result-ready latency over completed requests */
+} salt_serve_stats;
+
+int salt_serve_stats_get(salt_ctx *ctx, salt_serve_stats *out);
+
+/* ---------------------------------------------------------------- misc ---- */
+
+const char *salt_status_str(int status);
+const char *salt_last_error(const salt_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SALT_H */

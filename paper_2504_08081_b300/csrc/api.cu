@@ -1,0 +1,530 @@
+// C ABI entry points: model upload, planning, batch calls, options, errors.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "salt_internal.cuh"
+
+using namespace salt;
+
+namespace {
+
+// CGS constants for the bandpass weights: Planck (exact SI), c in A/s (exact),
+// the AB reference flux density 3631 Jy.
+constexpr double kPlanck = 6.62607015e-27;
+constexpr double kLightAA = 2.99792458e18;
+constexpr double kAB = 3631e-23;
+// SALT2 colour-law reference wavelengths.
+constexpr double kLamB = 4302.57, kLamV = 5428.55;
+
+int set_err(salt_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->last_error = msg;
+    }
+    return code;
+}
+
+int cuda_err(salt_ctx *ctx, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();  // the status code reports it: do not leave it for the caller's runtime
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? SALT_ERR_OOM : SALT_ERR_CUDA, m);
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, what); \
+    } while (0)
+
+double cl_poly(const double a[4], double x) {
+    const double lin = 1.0 - a[0] - a[1] - a[2] - a[3];
+    double xp = x, P = lin * x;
+    for (int q = 0; q < 4; ++q) { xp *= x; P += a[q] * xp; }
+    return P;
+}
+
+double cl_dpoly(const double a[4], double x) {
+    const double lin = 1.0 - a[0] - a[1] - a[2] - a[3];
+    double xp = 1.0, dP = lin;
+    for (int q = 0; q < 4; ++q) { xp *= x; dP += (q + 2) * a[q] * xp; }
+    return dP;
+}
+
+bool finite_all(const float *v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ model
+
+extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *bands, int32_t n_bands,
+                               int32_t device, size_t serve_mem_bytes, salt_ctx **out) {
+    if (!out) return SALT_ERR_INVALID;
+    *out = nullptr;
+    salt_ctx *ctx = nullptr;
+    if (!md || (!bands && n_bands > 0) || n_bands < 0 || n_bands > SALT_MAX_BANDS) return SALT_ERR_INVALID;
+    if (md->n_phase < 4 || md->n_wave < 4 || md->n_phase > 256 || !(md->dphase > 0) || !(md->dwave > 0) ||
+        !std::isfinite(md->phase0) || !std::isfinite(md->wave0) || !md->m0 || !md->m1 || md->n_cl != 4 ||
+        !md->cl || !(md->cl_lo < md->cl_hi))
+        return SALT_ERR_INVALID;
+    const size_t ng = (size_t)md->n_phase * md->n_wave;
+    if (!finite_all(md->m0, ng) || !finite_all(md->m1, ng)) return SALT_ERR_INVALID;
+    for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(md->cl[q])) return SALT_ERR_INVALID;
+    for (int b = 0; b < n_bands; ++b) {
+        const salt_band_desc &bd = bands[b];
+        if (bd.n < 2 || !bd.wave || !bd.trans) return SALT_ERR_INVALID;
+        for (int k = 0; k < bd.n; ++k) {
+            if (!std::isfinite(bd.wave[k]) || !std::isfinite(bd.trans[k]) || !(bd.wave[k] > 0)) return SALT_ERR_INVALID;
+            if (k > 0 && !(bd.wave[k] > bd.wave[k - 1])) return SALT_ERR_INVALID;
+        }
+    }
+    ctx = new (std::nothrow) salt_ctx();
+    if (!ctx) return SALT_ERR_OOM;
+    ctx->device = device;
+    ctx->host_cl.assign(md->cl, md->cl + 4);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete ctx; return SALT_ERR_CUDA; }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    ctx->num_sms = sms > 0 ? sms : 1;
+
+    ModelParams &mp = ctx->mp;
+    mp.n_phase = md->n_phase;
+    mp.n_wave = md->n_wave;
+    mp.phase0 = (float)md->phase0;
+    mp.inv_dphase = (float)(1.0 / md->dphase);
+    mp.phase_max = (float)(md->phase0 + (md->n_phase - 1) * md->dphase);
+    mp.wave0 = (float)md->wave0;
+    mp.inv_dwave = (float)(1.0 / md->dwave);
+    mp.wave_max = (float)(md->wave0 + (md->n_wave - 1) * md->dwave);
+    mp.dwave = (float)md->dwave;
+    const double a[4] = {md->cl[0], md->cl[1], md->cl[2], md->cl[3]};
+    mp.cl_p[0] = (float)(1.0 - a[0] - a[1] - a[2] - a[3]);
+    for (int q = 0; q < 4; ++q) mp.cl_p[q + 1] = (float)a[q];
+    const double span = kLamV - kLamB;
+    mp.cl_lamB = (float)kLamB;
+    mp.cl_inv_span = (float)(1.0 / span);
+    mp.cl_lo = (float)md->cl_lo;
+    mp.cl_hi = (float)md->cl_hi;
+    const double xlo = (md->cl_lo - kLamB) / span, xhi = (md->cl_hi - kLamB) / span;
+    mp.cl_xlo = (float)xlo;
+    mp.cl_Plo = (float)cl_poly(a, xlo);
+    mp.cl_dPlo = (float)cl_dpoly(a, xlo);
+    mp.cl_xhi = (float)xhi;
+    mp.cl_Phi = (float)cl_poly(a, xhi);
+    mp.cl_dPhi = (float)cl_dpoly(a, xhi);
+
+    // bandpass weights: trapezoid Delta_k, lambda T Delta / (h c), divided by
+    // the AB photon integral Z_b (FP64 on the host, then float32)
+    std::vector<float> lam_h, w_h;
+    mp.bands.n_bands = n_bands;
+    int off = 0;
+    const double hc = kPlanck * kLightAA;
+    for (int b = 0; b < n_bands; ++b) {
+        const salt_band_desc &bd = bands[b];
+        const int K = bd.n;
+        std::vector<double> wk(K);
+        double Z = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double lo = (k > 0) ? bd.wave[k - 1] : bd.wave[k];
+            const double hi = (k + 1 < K) ? bd.wave[k + 1] : bd.wave[k];
+            const double delta = 0.5 * (hi - lo);
+            wk[k] = bd.wave[k] * bd.trans[k] * delta / hc;
+            Z += wk[k] * kAB * kLightAA / (bd.wave[k] * bd.wave[k]);
+        }
+        if (!(Z > 0) || !std::isfinite(Z)) { delete ctx; return SALT_ERR_INVALID; }
+        mp.bands.off[b] = off;
+        mp.bands.n[b] = K;
+        mp.bands.lam_lo[b] = (float)bd.wave[0];
+        mp.bands.lam_hi[b] = (float)bd.wave[K - 1];
+        for (int k = 0; k < K; ++k) {
+            lam_h.push_back((float)bd.wave[k]);
+            w_h.push_back((float)(wk[k] / Z));
+        }
+        off += K;
+    }
+    std::vector<float2> g(ng);
+    for (size_t q = 0; q < ng; ++q) g[q] = make_float2(md->m0[q], md->m1[q]);
+
+    auto fail = [&](cudaError_t err, const char *what) {
+        int code = cuda_err(nullptr, err, what);
+        salt_destroy(ctx);
+        return code;
+    };
+    if ((e = cudaMalloc(&ctx->g01_d, ng * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc grid");
+    if ((e = cudaMemcpy(ctx->g01_d, g.data(), ng * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "upload grid");
+    const size_t nk = std::max<size_t>(lam_h.size(), 1);
+    if ((e = cudaMalloc(&ctx->band_lam_d, nk * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc bands");
+    if ((e = cudaMalloc(&ctx->band_w_d, nk * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc bands");
+    if (!lam_h.empty()) {
+        if ((e = cudaMemcpy(ctx->band_lam_d, lam_h.data(), lam_h.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e, "upload bands");
+        if ((e = cudaMemcpy(ctx->band_w_d, w_h.data(), w_h.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e, "upload bands");
+    }
+    if ((e = cudaMalloc(&ctx->err_d, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
+    if ((e = cudaMemset(ctx->err_d, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "memset err");
+    mp.g01 = ctx->g01_d;
+    mp.band_lam = ctx->band_lam_d;
+    mp.band_w = ctx->band_w_d;
+    ctx->serve_mem = serve_mem_bytes;
+    if (serve_mem_bytes > 0) {
+        ctx->serve = serve_create(ctx, serve_mem_bytes);
+        if (!ctx->serve) { salt_destroy(ctx); return SALT_ERR_OOM; }
+    }
+    *out = ctx;
+    return SALT_OK;
+}
+
+extern "C" void salt_destroy(salt_ctx *ctx) {
+    if (!ctx) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    if (ctx->serve) {
+        serve_destroy(ctx->serve);
+        ctx->serve = nullptr;
+    }
+    if (ctx->g01_d) cudaFree(ctx->g01_d);
+    if (ctx->band_lam_d) cudaFree(ctx->band_lam_d);
+    if (ctx->band_w_d) cudaFree(ctx->band_w_d);
+    if (ctx->err_d) cudaFree(ctx->err_d);
+    delete ctx;
+    cudaSetDevice(prev);
+    (void)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ planning
+
+namespace salt {
+
+static bool offsets_ok(int64_t n_sn, const int64_t *off) {
+    if (!off || off[0] != 0) return false;
+    for (int64_t s = 0; s < n_sn; ++s)
+        if (off[s + 1] < off[s]) return false;
+    return true;
+}
+
+static int default_tile(const salt_ctx *ctx, int64_t n_sn, int64_t n_par) {
+    if (ctx->tile_samples > 0) return ctx->tile_samples;
+    const double mean = n_sn > 0 ? (double)n_par / (double)n_sn : 1.0;
+    if (mean >= 8) return 8;
+    if (mean >= 4) return 4;
+    if (mean >= 2) return 2;
+    return 1;
+}
+
+int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off, int tile,
+               salt_plan *p, cudaStream_t st, bool async_alloc) {
+    if (n_sn < 0 || !offsets_ok(n_sn, obs_off) || !offsets_ok(n_sn, par_off))
+        return set_err(ctx, SALT_ERR_INVALID, "offsets must start at 0 and be nondecreasing");
+    for (int64_t s = 0; s < n_sn; ++s)
+        if (par_off[s + 1] - par_off[s] > INT32_MAX / 2)
+            return set_err(ctx, SALT_ERR_INVALID, "too many samples for one supernova");
+    p->ctx = ctx;
+    p->device = ctx->device;
+    p->n_sn = n_sn;
+    p->n_obs = obs_off[n_sn];
+    p->n_par = par_off[n_sn];
+    p->obs_off_h.assign(obs_off, obs_off + n_sn + 1);
+    p->par_off_h.assign(par_off, par_off + n_sn + 1);
+    p->bf_off_h.assign(n_sn + 1, 0);
+    for (int64_t s = 0; s < n_sn; ++s)
+        p->bf_off_h[s + 1] = p->bf_off_h[s] + (obs_off[s + 1] - obs_off[s]) * (par_off[s + 1] - par_off[s]);
+    p->n_bandflux = p->bf_off_h[n_sn];
+    if (tile <= 0) tile = default_tile(ctx, n_sn, p->n_par);
+    if (tile != 1 && tile != 2 && tile != 4 && tile != 8) tile = 8;
+    p->tile = tile;
+    // tiles per item: enough items to keep every SM busy and balanced
+    int64_t total_tiles = 0;
+    for (int64_t s = 0; s < n_sn; ++s) total_tiles += (par_off[s + 1] - par_off[s] + tile - 1) / tile;
+    int64_t target = (int64_t)ctx->num_sms * 16;
+    int tpi = (int)std::min<int64_t>(8, std::max<int64_t>(1, total_tiles / std::max<int64_t>(target, 1)));
+    p->tiles_per_item = tpi;
+    struct Cost { double c; WorkItem w; };
+    std::vector<Cost> items;
+    items.reserve((size_t)(total_tiles / tpi + n_sn + 1));
+    const int span = tile * tpi;
+    for (int64_t s = 0; s < n_sn; ++s) {
+        const int64_t S = par_off[s + 1] - par_off[s];
+        const int64_t n = obs_off[s + 1] - obs_off[s];
+        for (int64_t j0 = 0; j0 < S; j0 += span) {
+            const int nj = (int)std::min<int64_t>(span, S - j0);
+            const double cost = (double)((nj + tile - 1) / tile) * (64.0 + (double)n) * tile;
+            if (n > INT32_MAX) return set_err(ctx, SALT_ERR_INVALID, "too many observations for one supernova");
+            items.push_back({cost, WorkItem{obs_off[s], par_off[s] + j0, p->bf_off_h[s], (int32_t)n, nj,
+                                            (int32_t)j0, 0}});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Cost &x, const Cost &y) { return x.c > y.c; });
+    std::vector<WorkItem> wl(items.size());
+    for (size_t q = 0; q < items.size(); ++q) wl[q] = items[q].w;
+    p->n_items = (int)wl.size();
+    // device copies
+    auto alloc = [&](void **ptr, size_t bytes) -> cudaError_t {
+        bytes = std::max<size_t>(bytes, 16);
+        return async_alloc ? cudaMallocAsync(ptr, bytes, st) : cudaMalloc(ptr, bytes);
+    };
+    CK(alloc((void **)&p->obs_off_d, (n_sn + 1) * 8), "alloc offsets");
+    CK(alloc((void **)&p->par_off_d, (n_sn + 1) * 8), "alloc offsets");
+    CK(alloc((void **)&p->bf_off_d, (n_sn + 1) * 8), "alloc offsets");
+    CK(alloc((void **)&p->items_d, wl.size() * sizeof(WorkItem)), "alloc work list");
+    CK(alloc((void **)&p->counter_d, 16), "alloc counter");
+    CK(cudaMemcpyAsync(p->obs_off_d, obs_off, (n_sn + 1) * 8, cudaMemcpyHostToDevice, st), "upload offsets");
+    CK(cudaMemcpyAsync(p->par_off_d, par_off, (n_sn + 1) * 8, cudaMemcpyHostToDevice, st), "upload offsets");
+    CK(cudaMemcpyAsync(p->bf_off_d, p->bf_off_h.data(), (n_sn + 1) * 8, cudaMemcpyHostToDevice, st),
+       "upload offsets");
+    if (!wl.empty())
+        CK(cudaMemcpyAsync(p->items_d, wl.data(), wl.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
+           "upload work list");
+    // pageable sources: the copies above complete before return when not async
+    if (async_alloc) CK(cudaStreamSynchronize(st), "plan upload");
+    return SALT_OK;
+}
+
+void plan_free(salt_plan *p, cudaStream_t st) {
+    for (auto &kv : p->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    p->graphs.clear();
+    void *ptrs[] = {p->obs_off_d, p->par_off_d, p->bf_off_d, p->items_d, p->counter_d};
+    for (void *q : ptrs)
+        if (q) {
+            if (p->temporary) cudaFreeAsync(q, st); else cudaFree(q);
+        }
+    p->obs_off_d = p->par_off_d = p->bf_off_d = nullptr;
+    p->items_d = nullptr;
+    p->counter_d = nullptr;
+}
+
+int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *plan, const OutDev &o, int mode,
+              cudaStream_t st) {
+    cudaError_t e;
+    if (ctx->kernel == SALT_KERNEL_DIRECT)
+        e = launch_direct(ctx, b, o, mode, st);
+    else
+        e = launch_factorised(ctx, plan, b, o, mode, st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "kernel launch");
+    return SALT_OK;
+}
+
+}  // namespace salt
+
+extern "C" int salt_plan_create(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,
+                                salt_plan **out) {
+    if (!ctx || !out) return SALT_ERR_INVALID;
+    *out = nullptr;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    salt_plan *p = new (std::nothrow) salt_plan();
+    if (!p) return SALT_ERR_OOM;
+    int rc = plan_build(ctx, n_sn, obs_off, par_off, 0, p, 0, false);
+    if (rc == SALT_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_err(ctx, e, "plan upload");
+    }
+    if (rc != SALT_OK) {
+        plan_free(p, 0);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return SALT_OK;
+}
+
+extern "C" void salt_plan_destroy(salt_plan *plan) {
+    if (!plan) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(plan->device);
+    plan_free(plan, 0);
+    cudaSetDevice(prev);
+    (void)cudaGetLastError();
+    delete plan;
+}
+
+extern "C" int salt_bandflux_offsets(int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,
+                                     int64_t *bf_off) {
+    if (n_sn < 0 || !bf_off || !offsets_ok(n_sn, obs_off) || !offsets_ok(n_sn, par_off)) return SALT_ERR_INVALID;
+    bf_off[0] = 0;
+    for (int64_t s = 0; s < n_sn; ++s)
+        bf_off[s + 1] = bf_off[s] + (obs_off[s + 1] - obs_off[s]) * (par_off[s + 1] - par_off[s]);
+    return SALT_OK;
+}
+
+// ------------------------------------------------------------------ batch calls
+
+static int batch_call(salt_ctx *ctx, const salt_batch *bt, int mode, float *bf, double *chi2, float *grad,
+                      void *stream) {
+    if (!ctx || !bt) return SALT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (bt->n_sn < 0 || !bt->obs_off || !bt->par_off) return set_err(ctx, SALT_ERR_INVALID, "missing offsets");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const salt_plan *plan = bt->plan;
+    salt_plan tmp;
+    if (plan) {
+        if (plan->ctx != ctx || plan->n_sn != bt->n_sn ||
+            std::memcmp(plan->obs_off_h.data(), bt->obs_off, (bt->n_sn + 1) * 8) != 0 ||
+            std::memcmp(plan->par_off_h.data(), bt->par_off, (bt->n_sn + 1) * 8) != 0)
+            return set_err(ctx, SALT_ERR_INVALID, "plan does not match the batch offsets");
+    }
+    const int64_t n_obs = bt->n_sn ? bt->obs_off[bt->n_sn] : 0;
+    const int64_t n_par = bt->n_sn ? bt->par_off[bt->n_sn] : 0;
+    if (n_obs > 0 && (!bt->mjd || !bt->band || !bt->flux || !bt->fluxerr || !bt->zp))
+        return set_err(ctx, SALT_ERR_INVALID, "missing observation arrays");
+    if (n_par > 0 && (!bt->t0 || !bt->z || !bt->x0 || !bt->x1 || !bt->c))
+        return set_err(ctx, SALT_ERR_INVALID, "missing parameter arrays");
+    if (mode == MODE_BANDFLUX && !bf && n_par > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
+    if (mode != MODE_BANDFLUX && !chi2 && n_par > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
+    if (mode == MODE_GRAD && !grad && n_par > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
+    if (!plan) {
+        tmp.temporary = true;
+        int rc = plan_build(ctx, bt->n_sn, bt->obs_off, bt->par_off, 0, &tmp, st, true);
+        if (rc != SALT_OK) { plan_free(&tmp, st); return rc; }
+        plan = &tmp;
+    } else {
+        if (!offsets_ok(bt->n_sn, bt->obs_off) || !offsets_ok(bt->n_sn, bt->par_off))
+            return set_err(ctx, SALT_ERR_INVALID, "offsets must start at 0 and be nondecreasing");
+    }
+    BatchDev b{};
+    b.n_sn = bt->n_sn;
+    b.n_obs = n_obs;
+    b.n_par = n_par;
+    b.obs_off = plan->obs_off_d;
+    b.par_off = plan->par_off_d;
+    b.mjd = bt->mjd; b.band = bt->band; b.flux = bt->flux; b.fluxerr = bt->fluxerr; b.zp = bt->zp;
+    b.t0 = bt->t0; b.z = bt->z; b.x0 = bt->x0; b.x1 = bt->x1; b.c = bt->c;
+    int rc = SALT_OK;
+    if (bt->validate) {
+        cudaError_t e = cudaMemsetAsync(ctx->err_d + 1, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_validate(ctx, b, ctx->err_d + 1, st);
+        int flag = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, ctx->err_d + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_err(ctx, e, "validation");
+        else if (flag) rc = set_err(ctx, SALT_ERR_INVALID, (flag & ERRBIT_BAND) ? "band id out of range"
+                                                            : (flag & ERRBIT_SIGMA) ? "fluxerr must be > 0"
+                                                                                    : "non-finite value or z <= -1");
+    }
+    if (rc == SALT_OK) {
+        OutDev o{bf, plan->bf_off_d, chi2, grad, ctx->err_d};
+        rc = run_batch(ctx, b, plan, o, mode, st);
+    }
+    if (plan == &tmp) plan_free(&tmp, st);
+    return rc;
+}
+
+extern "C" int salt_bandflux(salt_ctx *ctx, const salt_batch *batch, float *out, void *cuda_stream) {
+    return batch_call(ctx, batch, MODE_BANDFLUX, out, nullptr, nullptr, cuda_stream);
+}
+
+extern "C" int salt_chi2(salt_ctx *ctx, const salt_batch *batch, double *chi2, void *cuda_stream) {
+    return batch_call(ctx, batch, MODE_CHI2, nullptr, chi2, nullptr, cuda_stream);
+}
+
+extern "C" int salt_chi2_grad(salt_ctx *ctx, const salt_batch *batch, double *chi2, float *grad,
+                              void *cuda_stream) {
+    return batch_call(ctx, batch, MODE_GRAD, nullptr, chi2, grad, cuda_stream);
+}
+
+extern "C" int salt_check(salt_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return SALT_ERR_INVALID;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), st), "clear error word");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (flag)
+        return set_err(ctx, SALT_ERR_DATA, (flag & ERRBIT_BAND) ? "a kernel met a band id out of range"
+                                           : (flag & ERRBIT_SIGMA) ? "a kernel met fluxerr <= 0"
+                                                                   : "a kernel met non-finite parameters");
+    return SALT_OK;
+}
+
+// ------------------------------------------------------------------ options
+
+extern "C" int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value) {
+    if (!ctx) return SALT_ERR_INVALID;
+    switch (option) {
+        case SALT_OPT_KERNEL:
+            if (value < 0 || value > 2) return SALT_ERR_INVALID;
+            ctx->kernel = (int)value;
+            return SALT_OK;
+        case SALT_OPT_TILE_SAMPLES:
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) return SALT_ERR_INVALID;
+            ctx->tile_samples = (int)value;
+            return SALT_OK;
+        case SALT_OPT_GRAPHS:
+            ctx->use_graphs = value ? 1 : 0;
+            return SALT_OK;
+        case SALT_OPT_SERVE_CHUNK:
+            if (value < 1 || value > 4096) return SALT_ERR_INVALID;
+            ctx->serve_chunk = (int)value;
+            return SALT_OK;
+    }
+    return SALT_ERR_INVALID;
+}
+
+extern "C" int salt_get_option(const salt_ctx *ctx, int32_t option, int64_t *value) {
+    if (!ctx || !value) return SALT_ERR_INVALID;
+    switch (option) {
+        case SALT_OPT_KERNEL: *value = ctx->kernel; return SALT_OK;
+        case SALT_OPT_TILE_SAMPLES: *value = ctx->tile_samples; return SALT_OK;
+        case SALT_OPT_GRAPHS: *value = ctx->use_graphs; return SALT_OK;
+        case SALT_OPT_SERVE_CHUNK: *value = ctx->serve_chunk; return SALT_OK;
+    }
+    return SALT_ERR_INVALID;
+}
+
+// ------------------------------------------------------------------ serving
+
+extern "C" int salt_serve_submit(salt_ctx *ctx, const salt_request *req, uint64_t *ticket) {
+    if (!ctx || !ctx->serve) return SALT_ERR_INVALID;
+    return serve_submit(ctx->serve, req, ticket);
+}
+
+extern "C" int salt_serve_poll(salt_ctx *ctx, uint64_t ticket, int32_t wait_ms, double *chi2, float *grad) {
+    if (!ctx || !ctx->serve) return SALT_ERR_INVALID;
+    return serve_poll(ctx->serve, ticket, wait_ms, chi2, grad);
+}
+
+extern "C" int salt_serve_cancel(salt_ctx *ctx, uint64_t ticket) {
+    if (!ctx || !ctx->serve) return SALT_ERR_INVALID;
+    return serve_cancel(ctx->serve, ticket);
+}
+
+extern "C" int salt_serve_stats_get(salt_ctx *ctx, salt_serve_stats *out) {
+    if (!ctx || !ctx->serve || !out) return SALT_ERR_INVALID;
+    return serve_stats(ctx->serve, out);
+}
+
+// ------------------------------------------------------------------ misc
+
+extern "C" const char *salt_status_str(int status) {
+    switch (status) {
+        case SALT_OK: return "ok";
+        case SALT_PENDING: return "pending";
+        case SALT_ERR_INVALID: return "invalid argument or data";
+        case SALT_ERR_OOM: return "out of memory";
+        case SALT_ERR_CUDA: return "CUDA error";
+        case SALT_ERR_TIMEOUT: return "timeout";
+        case SALT_ERR_NOT_FOUND: return "ticket not found";
+        case SALT_ERR_CANCELLED: return "cancelled";
+        case SALT_ERR_DATA: return "invalid batch data met by a kernel";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *salt_last_error(const salt_ctx *ctx) {
+    if (!ctx) return "no context";
+    return ctx->last_error.c_str();
+}

@@ -1,0 +1,137 @@
+// Per-element device arithmetic of the SALT photometry path (FP32).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "salt_internal.cuh"
+
+namespace salt {
+
+// Tap set of one interpolation axis: 4 consecutive nodes starting at `first`
+// (first in [0, n-4]), their weights and the weights' derivatives with respect
+// to the axis coordinate. Keys cubic convolution (a = -1/2) on interior
+// intervals; on the first / last interval the two end nodes carry the linear
+// weights and the other two carry 0; outside the axis every weight is 0.
+struct Taps4 {
+    int first;
+    float w[4];
+    float dw[4];
+};
+
+// Keys a = -1/2 weights of nodes (i-1, i, i+1, i+2) at fraction t of interval i,
+// expanded as polynomials in t (value and d/dt).
+__device__ __forceinline__ void keys_weights(float t, float w[4]) {
+    float t2 = t * t;
+    w[0] = t * fmaf(t, fmaf(-0.5f, t, 1.0f), -0.5f);
+    w[1] = fmaf(t2, fmaf(1.5f, t, -2.5f), 1.0f);
+    w[2] = t * fmaf(t, fmaf(-1.5f, t, 2.0f), 0.5f);
+    w[3] = t2 * fmaf(0.5f, t, -0.5f);
+}
+
+__device__ __forceinline__ void keys_dweights(float t, float d[4]) {
+    d[0] = fmaf(t, fmaf(-1.5f, t, 2.0f), -0.5f);
+    d[1] = t * fmaf(4.5f, t, -5.0f);
+    d[2] = fmaf(t, fmaf(-4.5f, t, 4.0f), 0.5f);
+    d[3] = t * fmaf(1.5f, t, -1.0f);
+}
+
+// Interval index and fraction of coordinate x on a uniform axis of n >= 4
+// nodes. Returns false outside [x0, xmax].
+__device__ __forceinline__ bool axis_locate(float x, float x0, float inv_dx, float xmax, int n,
+                                            int &i, float &t) {
+    if (!(x >= x0 && x <= xmax)) return false;
+    float u = (x - x0) * inv_dx;
+    i = __float2int_rd(u);
+    i = min(max(i, 0), n - 2);
+    t = u - (float)i;
+    return true;
+}
+
+// Weights (and optionally derivatives w.r.t. x) for a located interval.
+template <bool DERIV>
+__device__ __forceinline__ void axis_taps_from(int i, float t, int n, float inv_dx, Taps4 &tp) {
+    if (i == 0 || i == n - 2) {
+        tp.first = (i == 0) ? 0 : n - 4;
+        int o = (i == 0) ? 0 : 2;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) { tp.w[m] = 0.f; if (DERIV) tp.dw[m] = 0.f; }
+        tp.w[o] = 1.0f - t;
+        tp.w[o + 1] = t;
+        if (DERIV) { tp.dw[o] = -inv_dx; tp.dw[o + 1] = inv_dx; }
+    } else {
+        tp.first = i - 1;
+        keys_weights(t, tp.w);
+        if (DERIV) {
+            keys_dweights(t, tp.dw);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) tp.dw[m] *= inv_dx;
+        }
+    }
+}
+
+template <bool DERIV>
+__device__ __forceinline__ void axis_taps(float x, float x0, float inv_dx, float xmax, int n,
+                                          Taps4 &tp) {
+    int i;
+    float t;
+    if (!axis_locate(x, x0, inv_dx, xmax, n, i, t)) {
+        tp.first = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) { tp.w[m] = 0.f; if (DERIV) tp.dw[m] = 0.f; }
+        return;
+    }
+    axis_taps_from<DERIV>(i, t, n, inv_dx, tp);
+}
+
+// SALT2-form colour law CL(lambda) and dCL/dlambda (linear outside [cl_lo, cl_hi]).
+__device__ __forceinline__ float colour_law(const ModelParams &m, float lam, float &dcl) {
+    float x = (lam - m.cl_lamB) * m.cl_inv_span;
+    float P, dP;
+    if (lam < m.cl_lo) {
+        dP = m.cl_dPlo;
+        P = fmaf(dP, x - m.cl_xlo, m.cl_Plo);
+    } else if (lam > m.cl_hi) {
+        dP = m.cl_dPhi;
+        P = fmaf(dP, x - m.cl_xhi, m.cl_Phi);
+    } else {
+        const float *p = m.cl_p;
+        P = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, p[4], p[3]), p[2]), p[1]), p[0]);
+        dP = fmaf(x, fmaf(x, fmaf(x, fmaf(x, 5.f * p[4], 4.f * p[3]), 3.f * p[2]), 2.f * p[1]),
+                  p[0]);
+    }
+    dcl = -dP * m.cl_inv_span;
+    return -P;
+}
+
+// 0.4 * log2(10) split into a float head and tail (Cody-Waite style).
+constexpr float kZpHi = 1.3287712335586548f;
+constexpr float kZpLo = 4.3962899987093351e-09f;
+
+// 10^(0.4 zp) in FP32 with the exponent argument carried in two parts, so the
+// rounding of 0.4*log2(10)*zp (|arg| ~ 37) does not cost ~1e-6 relative.
+__device__ __forceinline__ float zp_scale(float zp) {
+    float th = zp * kZpHi;
+    float te = fmaf(zp, kZpHi, -th) + zp * kZpLo;  // exact product error + tail
+    float n = rintf(th);
+    float f = (th - n) + te;
+    return ldexpf(exp2f(f), (int)n);
+}
+
+// -0.4 * log2(10): colour factor 10^(-0.4 c CL) = exp2(kColour * c * CL).
+constexpr float kColour = -1.32877123795494492f;
+// -0.4 * ln(10): d/dc of log of the colour factor per unit CL.
+constexpr float kColourLn = -0.921034037197618f;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace salt

@@ -1,0 +1,160 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "salt.h"
+
+namespace salt {
+
+// Error bits a kernel records in the context's device error word.
+enum : int { ERRBIT_BAND = 1, ERRBIT_SIGMA = 2, ERRBIT_PARAM = 4, ERRBIT_WINDOW = 8 };
+
+// Band table passed by value to every kernel (fits the kernel parameter space).
+struct BandTable {
+    int n_bands;
+    int off[SALT_MAX_BANDS];  // first sample of band b in the flat arrays
+    int n[SALT_MAX_BANDS];    // samples in band b
+    float lam_lo[SALT_MAX_BANDS], lam_hi[SALT_MAX_BANDS];  // first / last observer wavelength
+};
+
+// Model constants in the form the kernels use (FP32, derived on the host in FP64).
+struct ModelParams {
+    int n_phase, n_wave;
+    float phase0, inv_dphase, phase_max;
+    float wave0, inv_dwave, wave_max, dwave;
+    // colour law: P(x) = sum_{m=1..5} p[m-1] x^m, x = (lambda - lamB) * inv_span
+    float cl_p[5];
+    float cl_lamB, cl_inv_span, cl_lo, cl_hi;
+    float cl_xlo, cl_Plo, cl_dPlo, cl_xhi, cl_Phi, cl_dPhi;
+    const float2 *__restrict__ g01;      // [n_phase][n_wave] interleaved (M0, M1)
+    const float *__restrict__ band_lam;  // flat band wavelengths (observer frame)
+    const float *__restrict__ band_w;    // flat weights lambda T Delta / (h c Z_b)
+    BandTable bands;
+};
+
+// Device view of a batch (all pointers device-resident).
+struct BatchDev {
+    int64_t n_sn, n_obs, n_par;
+    const int64_t *__restrict__ obs_off;
+    const int64_t *__restrict__ par_off;
+    const double *__restrict__ mjd;
+    const int32_t *__restrict__ band;
+    const float *__restrict__ flux;
+    const float *__restrict__ fluxerr;
+    const float *__restrict__ zp;
+    const double *__restrict__ t0;
+    const float *__restrict__ z;
+    const float *__restrict__ x0;
+    const float *__restrict__ x1;
+    const float *__restrict__ c;
+};
+
+enum Mode : int { MODE_BANDFLUX = 0, MODE_CHI2 = 1, MODE_GRAD = 2 };
+
+struct OutDev {
+    float *bandflux;                // [bf_off[n_sn]]
+    const int64_t *bf_off;          // [n_sn + 1]
+    double *chi2;                   // [n_par]
+    float *grad;                    // [n_par][5]
+    int *err;                       // sticky error word
+};
+
+// One unit of work for the fused factorised kernel: one supernova's
+// observations [obs0, obs0 + nobs) against parameter samples
+// [par0, par0 + nj); jloc0 is the local index of sample par0 within its
+// supernova and bf0 the supernova's first bandflux slot (bandflux mode).
+struct WorkItem {
+    int64_t obs0, par0, bf0;
+    int32_t nobs, nj, jloc0, pad;
+};
+
+struct Tuning {
+    int tile_samples = 8;    // samples per tile inside an item
+    int tiles_per_item = 1;  // tiles an item walks through (G-window reuse in L1)
+};
+
+}  // namespace salt
+
+struct salt_plan {
+    salt_ctx *ctx = nullptr;  // identity check only; never dereferenced after creation
+    int device = 0;
+    int64_t n_sn = 0, n_obs = 0, n_par = 0, n_bandflux = 0;
+    std::vector<int64_t> obs_off_h, par_off_h, bf_off_h;
+    int64_t *obs_off_d = nullptr, *par_off_d = nullptr, *bf_off_d = nullptr;
+    salt::WorkItem *items_d = nullptr;
+    int n_items = 0;
+    int tile = 0, tiles_per_item = 0;
+    int *counter_d = nullptr;  // dynamic work counter of the persistent kernel
+    bool temporary = false;
+    // captured CUDA graphs keyed by the launch signature
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::map<std::string, GraphEntry> graphs;
+};
+
+namespace salt {
+struct ServeEngine;
+}
+
+struct salt_ctx {
+    int device = 0;
+    int num_sms = 0;
+    salt::ModelParams mp{};
+    float2 *g01_d = nullptr;
+    float *band_lam_d = nullptr, *band_w_d = nullptr;
+    int *err_d = nullptr;
+    std::string last_error;
+    int kernel = SALT_KERNEL_AUTO;
+    int tile_samples = 0;  // 0 = autotuned
+    int use_graphs = 1;
+    int serve_chunk = 64;
+    std::vector<double> host_cl;  // colour-law coefficients (for serving validation)
+    salt::ServeEngine *serve = nullptr;
+    size_t serve_mem = 0;
+    std::mutex mu;  // guards last_error for serve_* callers
+};
+
+namespace salt {
+
+// Launchers (kernels.cu).
+cudaError_t launch_direct(const salt_ctx *ctx, const BatchDev &b, const OutDev &o, int mode,
+                          cudaStream_t st);
+cudaError_t launch_factorised(const salt_ctx *ctx, const salt_plan *plan, const BatchDev &b,
+                              const OutDev &o, int mode, cudaStream_t st);
+cudaError_t launch_factorised_items(const salt_ctx *ctx, int tile, const WorkItem *items_d, int n_items,
+                                    int *counter_d, const BatchDev &b, const OutDev &o, int mode,
+                                    cudaStream_t st);
+cudaError_t launch_validate(const salt_ctx *ctx, const BatchDev &b, int *flag, cudaStream_t st);
+int factorised_smem_bytes(int tile, int mode);
+int factorised_max_tile();
+
+// Serving engine (serve.cu).
+ServeEngine *serve_create(salt_ctx *ctx, size_t mem_limit);
+void serve_destroy(ServeEngine *e);
+int serve_submit(ServeEngine *e, const salt_request *req, uint64_t *ticket);
+int serve_poll(ServeEngine *e, uint64_t ticket, int32_t wait_ms, double *chi2, float *grad);
+int serve_cancel(ServeEngine *e, uint64_t ticket);
+int serve_stats(ServeEngine *e, salt_serve_stats *out);
+
+// Host helpers (api.cu).
+int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,
+               int tile, salt_plan *p, cudaStream_t st, bool async_alloc);
+void plan_free(salt_plan *p, cudaStream_t st);
+int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *plan, const OutDev &o, int mode,
+              cudaStream_t st);
+
+}  // namespace salt

@@ -1,0 +1,542 @@
+// Serving engine: continuous batching of chi^2 / chi^2+gradient requests.
+//
+// Requests (one supernova each, any number of samples) are copied at submit,
+// queued, and admitted while their observations and samples fit the device
+// arenas (memory admission). The arenas are structure-of-arrays: every
+// observation array (mjd, band, flux, fluxerr, zp) shares one element index
+// space and every sample array (t0, z, x0, x1, c, chi2, grad) another, so one
+// work item addresses a request's data with a single element offset. A
+// scheduler thread turns the admitted requests' fixed-size sample chunks into
+// one ragged work list per (mode, tile) and launches the fused factorised
+// kernel over it; requests that arrive while earlier launches run on the GPU
+// join the next one. Uploads, kernels and downloads run on three streams
+// ordered by events, so copies overlap other requests' kernels. A request's
+// chunks go through exactly the same per-item code whatever else shares the
+// launch, so its results are bitwise identical alone and in a mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <list>
+
+#include "salt_internal.cuh"
+
+namespace salt {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(Clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over element range [0, size) with a coalescing free list.
+class RangeAlloc {
+  public:
+    explicit RangeAlloc(size_t size) : size_(size) {
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t n, size_t &off) {
+        n = std::max<size_t>(n, 1);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                off = it->first;
+                const size_t rest = it->second - n, noff = it->first + n;
+                free_.erase(it);
+                if (rest) free_[noff] = rest;
+                used_ += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = std::max<size_t>(n, 1);
+        used_ -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+    size_t size() const { return size_; }
+
+  private:
+    size_t size_, used_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+enum class St { QUEUED, ACTIVE, COPYING, DONE, CANCELLED, FAILED };
+
+struct Req {
+    uint64_t ticket = 0;
+    int n_obs = 0, n_par = 0;
+    bool grad = false;
+    int tile = 1;
+    size_t oo = SIZE_MAX, po = SIZE_MAX;  // element offsets in the observation / sample arenas
+    St st = St::QUEUED;
+    bool cancel = false;
+    bool launched = false;
+    int inflight = 0;  // launches referencing this request that have not completed
+    double t_submit = 0, t_done = 0;
+    std::vector<double> mjd, t0, chi2;  // inputs until admitted; chi2 = result
+    std::vector<int32_t> band;
+    std::vector<float> flux, fluxerr, zp, z, x0, x1, c, gout;  // gout = gradient result
+    cudaEvent_t ev_down = nullptr;
+};
+
+struct Launch {
+    cudaEvent_t ev = nullptr;
+    std::vector<uint64_t> reqs;
+    int slot = -1;
+};
+
+constexpr int kSlots = 16;          // item-list buffers (launch groups in flight)
+constexpr int kMaxItems = 1 << 15;  // items per launch group
+
+// bytes one observation / one sample occupies across all arrays
+constexpr size_t kObsBytes = 8 + 4 * 4;        // mjd, band, flux, fluxerr, zp
+constexpr size_t kParBytes = 8 + 4 * 4 + 8 + 20;  // t0, z, x0, x1, c, chi2, grad[5]
+
+}  // namespace
+
+struct ServeEngine {
+    salt_ctx *ctx = nullptr;
+    RangeAlloc obs_a, par_a;
+    // device arrays (SoA) and their pinned host mirrors
+    double *d_mjd = nullptr, *d_t0 = nullptr, *d_chi2 = nullptr;
+    int32_t *d_band = nullptr;
+    float *d_flux = nullptr, *d_fluxerr = nullptr, *d_zp = nullptr, *d_z = nullptr, *d_x0 = nullptr,
+          *d_x1 = nullptr, *d_c = nullptr, *d_grad = nullptr;
+    double *h_chi2 = nullptr;
+    float *h_grad = nullptr;
+    cudaStream_t s_up = nullptr, s_comp = nullptr, s_down = nullptr;
+    cudaEvent_t ev_up = nullptr;
+    WorkItem *items_d[kSlots] = {};
+    WorkItem *items_h[kSlots] = {};
+    int *counters_d = nullptr;
+    bool slot_busy[kSlots] = {};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+    std::list<Launch> inflight;
+    std::vector<double> lat_ms;
+    uint64_t next_ticket = 1;
+    uint64_t n_submitted = 0, n_completed = 0, n_cancelled = 0, n_rejected = 0, n_launches = 0;
+    bool stop = false;
+    std::string fatal;
+    std::thread th;
+
+    ServeEngine(size_t obs_cap, size_t par_cap) : obs_a(obs_cap), par_a(par_cap) {}
+};
+
+namespace {
+
+void fail_all(ServeEngine *e, const std::string &why) {
+    e->fatal = why;
+    for (auto &kv : e->reqs)
+        if (kv.second->st != St::DONE && kv.second->st != St::CANCELLED) kv.second->st = St::FAILED;
+    e->cv_done.notify_all();
+}
+
+void release_req(ServeEngine *e, Req &r) {
+    if (r.oo != SIZE_MAX) e->obs_a.release(r.oo, (size_t)r.n_obs);
+    if (r.po != SIZE_MAX) e->par_a.release(r.po, (size_t)r.n_par);
+    r.oo = r.po = SIZE_MAX;
+    if (r.ev_down) cudaEventDestroy(r.ev_down);
+    r.ev_down = nullptr;
+}
+
+int tile_for(int n_par) {
+    if (n_par >= 8) return 8;
+    if (n_par >= 4) return 4;
+    if (n_par >= 2) return 2;
+    return 1;
+}
+
+template <class T>
+cudaError_t up(T *dst, const std::vector<T> &src, size_t off, cudaStream_t st) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst + off, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// One scheduler iteration, lock held. Returns false after a CUDA error.
+bool tick(ServeEngine *e) {
+    cudaError_t err;
+    // 1. retire finished launches; queue result downloads of finished requests
+    for (auto it = e->inflight.begin(); it != e->inflight.end();) {
+        err = cudaEventQuery(it->ev);
+        if (err == cudaErrorNotReady) { ++it; continue; }
+        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+        for (uint64_t t : it->reqs) {
+            auto rq = e->reqs.find(t);
+            if (rq == e->reqs.end()) continue;
+            Req &r = *rq->second;
+            if (--r.inflight > 0) continue;
+            if (r.cancel) {
+                release_req(e, r);
+                r.st = St::CANCELLED;
+                e->cv_done.notify_all();
+                continue;
+            }
+            err = cudaMemcpyAsync(e->h_chi2 + r.po, e->d_chi2 + r.po, 8 * (size_t)r.n_par,
+                                  cudaMemcpyDeviceToHost, e->s_down);
+            if (err == cudaSuccess && r.grad)
+                err = cudaMemcpyAsync(e->h_grad + 5 * r.po, e->d_grad + 5 * r.po, 20 * (size_t)r.n_par,
+                                      cudaMemcpyDeviceToHost, e->s_down);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&r.ev_down, cudaEventDisableTiming);
+            if (err == cudaSuccess) err = cudaEventRecord(r.ev_down, e->s_down);
+            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+            r.st = St::COPYING;
+        }
+        cudaEventDestroy(it->ev);
+        e->slot_busy[it->slot] = false;
+        it = e->inflight.erase(it);
+    }
+    // 2. finished downloads -> results to the request, release its arena ranges
+    for (auto &kv : e->reqs) {
+        Req &r = *kv.second;
+        if (r.st != St::COPYING) continue;
+        err = cudaEventQuery(r.ev_down);
+        if (err == cudaErrorNotReady) continue;
+        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+        r.t_done = now_ms();
+        r.chi2.assign(e->h_chi2 + r.po, e->h_chi2 + r.po + r.n_par);
+        if (r.grad) r.gout.assign(e->h_grad + 5 * r.po, e->h_grad + 5 * (r.po + r.n_par));
+        release_req(e, r);
+        r.st = r.cancel ? St::CANCELLED : St::DONE;
+        if (r.st == St::DONE) {
+            e->lat_ms.push_back(r.t_done - r.t_submit);
+            e->n_completed++;
+        }
+        e->cv_done.notify_all();
+    }
+    // 3. admit queued requests while both arenas have room (FIFO)
+    bool uploaded = false;
+    while (!e->queue.empty()) {
+        auto rq = e->reqs.find(e->queue.front());
+        if (rq == e->reqs.end() || rq->second->st != St::QUEUED) { e->queue.pop_front(); continue; }
+        Req &r = *rq->second;
+        size_t oo = SIZE_MAX, po = SIZE_MAX;
+        if (!e->par_a.alloc((size_t)r.n_par, po)) break;
+        if (!e->obs_a.alloc((size_t)r.n_obs, oo)) { e->par_a.release(po, (size_t)r.n_par); break; }
+        r.oo = oo;
+        r.po = po;
+        // pageable sources: each copy is staged by the driver before the call returns
+        err = up(e->d_mjd, r.mjd, oo, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_band, r.band, oo, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_flux, r.flux, oo, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_fluxerr, r.fluxerr, oo, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_zp, r.zp, oo, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_t0, r.t0, po, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_z, r.z, po, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_x0, r.x0, po, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_x1, r.x1, po, e->s_up);
+        if (err == cudaSuccess) err = up(e->d_c, r.c, po, e->s_up);
+        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+        std::vector<double>().swap(r.mjd);
+        std::vector<double>().swap(r.t0);
+        std::vector<int32_t>().swap(r.band);
+        for (auto *v : {&r.flux, &r.fluxerr, &r.zp, &r.z, &r.x0, &r.x1, &r.c}) std::vector<float>().swap(*v);
+        r.st = St::ACTIVE;
+        uploaded = true;
+        e->queue.pop_front();
+    }
+    if (uploaded) {
+        err = cudaEventRecord(e->ev_up, e->s_up);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->s_comp, e->ev_up, 0);
+        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+    }
+    // 4. one launch per (mode, tile) over the admitted requests not yet launched
+    const int chunk = std::max(1, e->ctx->serve_chunk);
+    BatchDev b{};
+    b.mjd = e->d_mjd; b.band = e->d_band; b.flux = e->d_flux; b.fluxerr = e->d_fluxerr; b.zp = e->d_zp;
+    b.t0 = e->d_t0; b.z = e->d_z; b.x0 = e->d_x0; b.x1 = e->d_x1; b.c = e->d_c;
+    OutDev o{nullptr, nullptr, e->d_chi2, e->d_grad, e->ctx->err_d};
+    for (int mode = MODE_CHI2; mode <= MODE_GRAD; ++mode) {
+        for (int tile : {1, 2, 4, 8}) {
+            int slot = -1;
+            for (int q = 0; q < kSlots; ++q)
+                if (!e->slot_busy[q]) { slot = q; break; }
+            if (slot < 0) return true;  // all item buffers in flight: next tick
+            std::vector<uint64_t> members;
+            int n_items = 0;
+            for (auto &kv : e->reqs) {
+                Req &r = *kv.second;
+                if (r.st != St::ACTIVE || r.launched || r.cancel) continue;
+                if ((r.grad ? MODE_GRAD : MODE_CHI2) != mode || r.tile != tile) continue;
+                const int need = (r.n_par + chunk - 1) / chunk;
+                if (n_items + need > kMaxItems) continue;
+                for (int j0 = 0; j0 < r.n_par; j0 += chunk) {
+                    WorkItem w{};
+                    w.obs0 = (int64_t)r.oo;
+                    w.par0 = (int64_t)r.po + j0;
+                    w.bf0 = 0;
+                    w.nobs = r.n_obs;
+                    w.nj = std::min(chunk, r.n_par - j0);
+                    w.jloc0 = j0;
+                    e->items_h[slot][n_items++] = w;
+                }
+                members.push_back(r.ticket);
+            }
+            if (members.empty()) continue;
+            Launch L;
+            L.slot = slot;
+            L.reqs = members;
+            err = cudaMemcpyAsync(e->items_d[slot], e->items_h[slot], (size_t)n_items * sizeof(WorkItem),
+                                  cudaMemcpyHostToDevice, e->s_comp);
+            if (err == cudaSuccess)
+                err = launch_factorised_items(e->ctx, tile, e->items_d[slot], n_items, e->counters_d + 4 * slot,
+                                              b, o, mode, e->s_comp);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+            if (err == cudaSuccess) err = cudaEventRecord(L.ev, e->s_comp);
+            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+            e->slot_busy[slot] = true;
+            e->n_launches++;
+            for (uint64_t t : members) {
+                Req &r = *e->reqs[t];
+                r.launched = true;
+                r.inflight = 1;
+            }
+            e->inflight.push_back(std::move(L));
+        }
+    }
+    return true;
+}
+
+bool has_work(ServeEngine *e) {
+    if (!e->inflight.empty() || !e->queue.empty()) return true;
+    for (auto &kv : e->reqs) {
+        const Req &r = *kv.second;
+        if (r.st == St::COPYING || (r.st == St::ACTIVE && !r.launched)) return true;
+    }
+    return false;
+}
+
+void run(ServeEngine *e) {
+    cudaSetDevice(e->ctx->device);
+    std::unique_lock<std::mutex> lk(e->mu);
+    while (!e->stop) {
+        if (!e->fatal.empty()) {
+            e->cv_work.wait(lk, [&] { return e->stop; });
+            break;
+        }
+        if (!has_work(e)) {
+            e->cv_work.wait(lk);
+            continue;
+        }
+        tick(e);
+        if (has_work(e)) e->cv_work.wait_for(lk, std::chrono::microseconds(20));
+    }
+}
+
+}  // namespace
+
+ServeEngine *serve_create(salt_ctx *ctx, size_t mem_limit) {
+    // split the budget: half observations, half samples
+    const size_t obs_cap = std::max<size_t>(mem_limit / 2 / kObsBytes, 1024);
+    const size_t par_cap = std::max<size_t>(mem_limit / 2 / kParBytes, 1024);
+    auto *e = new (std::nothrow) ServeEngine(obs_cap, par_cap);
+    if (!e) return nullptr;
+    e->ctx = ctx;
+    bool ok = true;
+    auto dm = [&](void **p, size_t bytes) { if (ok) ok = cudaMalloc(p, bytes) == cudaSuccess; };
+    dm((void **)&e->d_mjd, 8 * obs_cap);
+    dm((void **)&e->d_band, 4 * obs_cap);
+    dm((void **)&e->d_flux, 4 * obs_cap);
+    dm((void **)&e->d_fluxerr, 4 * obs_cap);
+    dm((void **)&e->d_zp, 4 * obs_cap);
+    dm((void **)&e->d_t0, 8 * par_cap);
+    dm((void **)&e->d_z, 4 * par_cap);
+    dm((void **)&e->d_x0, 4 * par_cap);
+    dm((void **)&e->d_x1, 4 * par_cap);
+    dm((void **)&e->d_c, 4 * par_cap);
+    dm((void **)&e->d_chi2, 8 * par_cap);
+    dm((void **)&e->d_grad, 20 * par_cap);
+    dm((void **)&e->counters_d, 4 * sizeof(int) * kSlots);
+    if (ok) ok = cudaHostAlloc(&e->h_chi2, 8 * par_cap, cudaHostAllocDefault) == cudaSuccess;
+    if (ok) ok = cudaHostAlloc(&e->h_grad, 20 * par_cap, cudaHostAllocDefault) == cudaSuccess;
+    if (ok) ok = cudaStreamCreateWithFlags(&e->s_up, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaStreamCreateWithFlags(&e->s_comp, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaStreamCreateWithFlags(&e->s_down, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&e->ev_up, cudaEventDisableTiming) == cudaSuccess;
+    for (int q = 0; ok && q < kSlots; ++q) {
+        dm((void **)&e->items_d[q], kMaxItems * sizeof(WorkItem));
+        if (ok) ok = cudaHostAlloc(&e->items_h[q], kMaxItems * sizeof(WorkItem), cudaHostAllocDefault) == cudaSuccess;
+    }
+    if (!ok) {
+        serve_destroy(e);
+        return nullptr;
+    }
+    e->th = std::thread(run, e);
+    return e;
+}
+
+void serve_destroy(ServeEngine *e) {
+    if (!e) return;
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->stop = true;
+    }
+    e->cv_work.notify_all();
+    e->cv_done.notify_all();
+    if (e->th.joinable()) e->th.join();
+    for (cudaStream_t s : {e->s_up, e->s_comp, e->s_down})
+        if (s) cudaStreamSynchronize(s);
+    for (auto &L : e->inflight)
+        if (L.ev) cudaEventDestroy(L.ev);
+    for (auto &kv : e->reqs)
+        if (kv.second->ev_down) cudaEventDestroy(kv.second->ev_down);
+    for (int q = 0; q < kSlots; ++q) {
+        if (e->items_d[q]) cudaFree(e->items_d[q]);
+        if (e->items_h[q]) cudaFreeHost(e->items_h[q]);
+    }
+    void *dptrs[] = {e->d_mjd, e->d_band, e->d_flux, e->d_fluxerr, e->d_zp, e->d_t0, e->d_z, e->d_x0,
+                     e->d_x1, e->d_c, e->d_chi2, e->d_grad, e->counters_d};
+    for (void *p : dptrs)
+        if (p) cudaFree(p);
+    if (e->h_chi2) cudaFreeHost(e->h_chi2);
+    if (e->h_grad) cudaFreeHost(e->h_grad);
+    if (e->ev_up) cudaEventDestroy(e->ev_up);
+    for (cudaStream_t s : {e->s_up, e->s_comp, e->s_down})
+        if (s) cudaStreamDestroy(s);
+    delete e;
+}
+
+int serve_submit(ServeEngine *e, const salt_request *q, uint64_t *ticket) {
+    if (!q || !ticket || q->n_obs < 0 || q->n_par < 1) return SALT_ERR_INVALID;
+    const int n = q->n_obs, S = q->n_par;
+    if (n > 0 && (!q->mjd || !q->band || !q->flux || !q->fluxerr || !q->zp)) return SALT_ERR_INVALID;
+    if (!q->t0 || !q->z || !q->x0 || !q->x1 || !q->c) return SALT_ERR_INVALID;
+    const int nb = e->ctx->mp.bands.n_bands;
+    for (int i = 0; i < n; ++i)
+        if (q->band[i] < 0 || q->band[i] >= nb || !(q->fluxerr[i] > 0.f) || !std::isfinite(q->fluxerr[i]) ||
+            !std::isfinite(q->mjd[i]) || !std::isfinite(q->flux[i]) || !std::isfinite(q->zp[i]))
+            return SALT_ERR_INVALID;
+    for (int j = 0; j < S; ++j)
+        if (!std::isfinite(q->t0[j]) || !std::isfinite(q->z[j]) || !(q->z[j] > -1.f) || !std::isfinite(q->x0[j]) ||
+            !std::isfinite(q->x1[j]) || !std::isfinite(q->c[j]))
+            return SALT_ERR_INVALID;
+    if ((size_t)n > e->obs_a.size() || (size_t)S > e->par_a.size()) {
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->n_rejected++;
+        return SALT_ERR_OOM;
+    }
+    auto r = std::make_unique<Req>();
+    r->n_obs = n;
+    r->n_par = S;
+    r->grad = q->want_grad != 0;
+    r->tile = tile_for(S);
+    r->mjd.assign(q->mjd, q->mjd + n);
+    r->band.assign(q->band, q->band + n);
+    r->flux.assign(q->flux, q->flux + n);
+    r->fluxerr.assign(q->fluxerr, q->fluxerr + n);
+    r->zp.assign(q->zp, q->zp + n);
+    r->t0.assign(q->t0, q->t0 + S);
+    r->z.assign(q->z, q->z + S);
+    r->x0.assign(q->x0, q->x0 + S);
+    r->x1.assign(q->x1, q->x1 + S);
+    r->c.assign(q->c, q->c + S);
+    r->t_submit = now_ms();
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        if (!e->fatal.empty()) return SALT_ERR_CUDA;
+        if (e->stop) return SALT_ERR_CANCELLED;
+        r->ticket = e->next_ticket++;
+        *ticket = r->ticket;
+        e->queue.push_back(r->ticket);
+        e->reqs.emplace(r->ticket, std::move(r));
+        e->n_submitted++;
+    }
+    e->cv_work.notify_one();
+    return SALT_OK;
+}
+
+int serve_poll(ServeEngine *e, uint64_t ticket, int32_t wait_ms, double *chi2, float *grad) {
+    std::unique_lock<std::mutex> lk(e->mu);
+    auto it = e->reqs.find(ticket);
+    if (it == e->reqs.end()) return SALT_ERR_NOT_FOUND;
+    Req *rp = it->second.get();
+    auto ready = [rp] { return rp->st == St::DONE || rp->st == St::CANCELLED || rp->st == St::FAILED; };
+    if (!ready()) {
+        if (wait_ms == 0) return SALT_PENDING;
+        if (wait_ms < 0)
+            e->cv_done.wait(lk, ready);
+        else if (!e->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), ready))
+            return SALT_ERR_TIMEOUT;
+    }
+    int rc = SALT_OK;
+    if (rp->st == St::CANCELLED) rc = SALT_ERR_CANCELLED;
+    else if (rp->st == St::FAILED) rc = SALT_ERR_CUDA;
+    else {
+        if (chi2) std::memcpy(chi2, rp->chi2.data(), 8 * (size_t)rp->n_par);
+        if (grad && rp->grad) std::memcpy(grad, rp->gout.data(), 20 * (size_t)rp->n_par);
+    }
+    e->reqs.erase(ticket);
+    return rc;
+}
+
+int serve_cancel(ServeEngine *e, uint64_t ticket) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    auto it = e->reqs.find(ticket);
+    if (it == e->reqs.end()) return SALT_ERR_NOT_FOUND;
+    Req &r = *it->second;
+    if (r.st == St::DONE || r.st == St::FAILED || r.st == St::CANCELLED) return SALT_OK;
+    if (!r.cancel) e->n_cancelled++;
+    r.cancel = true;
+    if (r.st == St::QUEUED) {
+        r.st = St::CANCELLED;
+        e->cv_done.notify_all();
+    } else if (r.st == St::ACTIVE && !r.launched) {
+        // its upload may still be in flight: drain the upload stream first
+        cudaStreamSynchronize(e->s_up);
+        release_req(e, r);
+        r.st = St::CANCELLED;
+        e->cv_done.notify_all();
+    }
+    // launched: released when its launch retires (tick)
+    return SALT_OK;
+}
+
+int serve_stats(ServeEngine *e, salt_serve_stats *out) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = e->n_submitted;
+    out->completed = e->n_completed;
+    out->cancelled = e->n_cancelled;
+    out->rejected = e->n_rejected;
+    out->launches = e->n_launches;
+    out->queued = e->queue.size();
+    uint64_t act = 0;
+    for (auto &kv : e->reqs)
+        if (kv.second->st == St::ACTIVE || kv.second->st == St::COPYING) act++;
+    out->active = act;
+    out->mem_in_use = e->obs_a.used() * kObsBytes + e->par_a.used() * kParBytes;
+    out->mem_limit = e->obs_a.size() * kObsBytes + e->par_a.size() * kParBytes;
+    if (!e->lat_ms.empty()) {
+        std::vector<double> v = e->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const double pos = q * (double)(v.size() - 1);
+            const size_t lo = (size_t)pos;
+            const size_t hi = std::min(lo + 1, v.size() - 1);
+            return v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+    }
+    return SALT_OK;
+}
+
+}  // namespace salt

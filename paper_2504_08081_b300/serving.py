@@ -1,0 +1,130 @@
+"""Serving client: replay a stream of chi^2 / chi^2+gradient requests against
+the library's continuous-batching engine (salt_serve_submit / poll), and the
+same stream as plain per-request launches for comparison.
+
+Latency is the engine's own submit -> results-on-host time (steady clock in
+the library); throughput is completed requests over the replay's wall time.
+"""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+
+from . import _abi
+from .torch_api import Salt
+
+
+def _req_arrays(rq):
+    b = rq.batch
+    return dict(n_obs=b.n_obs, mjd=b.mjd, band=b.band, flux=b.flux, fluxerr=b.fluxerr, zp=b.zp,
+                t0=b.t0, z=b.z, x0=b.x0, x1=b.x1, c=b.c, want_grad=rq.want_grad)
+
+
+def replay(salt: Salt, requests, arrivals_s=None, collect=True):
+    """Submit requests (at their arrival times when given, else all at once),
+    wait for every result. Returns (wall seconds, results list, stats dict)."""
+    n = len(requests)
+    tickets = [None] * n
+    results = [None] * n
+    done = threading.Event()
+    errors = []
+
+    def poller():
+        try:
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(0)
+                rq = requests[i]
+                rc, x2, g = salt.poll(tickets[i], rq.batch.n_par, rq.want_grad, wait_ms=-1)
+                if rc != _abi.SALT_OK:
+                    errors.append((i, rc))
+                if collect:
+                    results[i] = (x2, g)
+        except Exception as ex:  # pragma: no cover - surfaced below
+            errors.append(("poller", repr(ex)))
+        done.set()
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for i, rq in enumerate(requests):
+        if arrivals_s is not None:
+            target = t0 + arrivals_s[i]
+            while True:
+                dt = target - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+        tickets[i] = salt.submit(**_req_arrays(rq))
+    done.wait()
+    wall = time.perf_counter() - t0
+    th.join()
+    if errors:
+        raise RuntimeError(f"serving errors: {errors[:5]}")
+    return wall, results, salt.serve_stats()
+
+
+def plain_per_request(salt: Salt, requests, limit_s: float = 20.0):
+    """Each request alone: its own upload, one launch, result download, sync.
+    Returns (requests done, wall seconds, per-request latency ms)."""
+    import torch
+    lat = []
+    t0 = time.perf_counter()
+    k = 0
+    for rq in requests:
+        s0 = time.perf_counter()
+        db = salt.upload(rq.batch, plan=False)
+        if rq.want_grad:
+            x2, g = salt.chi2_grad(db)
+            x2.cpu(), g.cpu()
+        else:
+            salt.chi2(db).cpu()
+        torch.cuda.current_stream().synchronize()
+        lat.append(1e3 * (time.perf_counter() - s0))
+        k += 1
+        if time.perf_counter() - t0 > limit_s:
+            break
+    return k, time.perf_counter() - t0, lat
+
+
+def run_serving_bench(device: int = 0, n_req: int = 20000, seed: int = 1004,
+                      rates=(0.5, 0.8, 0.95), serve_mem: int = 512 << 20, max_replay_s: float = 8.0):
+    """Saturated throughput, Poisson replays at fractions of it, and the
+    plain per-request baseline on the same request stream."""
+    import workloads as W
+    wl = W.config4(seed=seed, n_req=n_req)
+    reqs = wl.requests
+    out = {"requests": len(reqs),
+           "samples_total": int(sum(r.batch.n_par for r in reqs)),
+           "bandfluxes_total": int(sum(r.batch.n_par * r.batch.n_obs for r in reqs))}
+    # saturated: everything submitted at once
+    s = Salt(wl.model, wl.bands, device=device, serve_mem_bytes=serve_mem)
+    wall, _, st = replay(s, reqs, None, collect=False)
+    sat = len(reqs) / wall
+    out["saturated"] = {"req_per_s": sat, "bandfluxes_per_s": out["bandfluxes_total"] / wall,
+                        "wall_s": wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                        "launches": st["launches"]}
+    s.close()
+    rng = np.random.default_rng(seed + 1)
+    for fr in rates:
+        rate = fr * sat
+        n = int(min(len(reqs), max(200, rate * max_replay_s)))
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        s = Salt(wl.model, wl.bands, device=device, serve_mem_bytes=serve_mem)
+        wall, _, st = replay(s, reqs[:n], arr, collect=False)
+        out[f"poisson_{fr:.2f}"] = {"offered_req_per_s": rate, "served_req_per_s": n / wall,
+                                     "requests": n, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                                     "launches": st["launches"]}
+        s.close()
+    # plain per-request launches on the same stream (closed loop, bounded time)
+    s = Salt(wl.model, wl.bands, device=device)
+    k, wall, lat = plain_per_request(s, reqs, limit_s=max_replay_s)
+    out["plain_per_request"] = {"req_per_s": k / wall, "requests": k,
+                                "p50_ms": float(np.percentile(lat, 50)),
+                                "p99_ms": float(np.percentile(lat, 99))}
+    out["batched_vs_plain_throughput"] = sat / (k / wall)
+    s.close()
+    return out

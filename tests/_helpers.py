@@ -1,0 +1,88 @@
+"""Shared test helpers: workloads with observed fluxes made by the FP64 oracle
+at the truth (plus seeded noise), tolerances, and comparisons."""
+import numpy as np
+
+import oracle
+import workloads as W
+
+# Tolerances (FP32 kernel vs FP64 oracle).
+BF_RTOL = 1e-5          # bandflux, relative
+BF_FLOOR = 1e-3         # ... relative to max(|B|, BF_FLOOR * max |B| of the supernova)
+GRAD_RTOL = 1e-3        # gradient, against the scaled gradient's inf-norm per sample
+SCALES = (0.01, 1.0, None, 1.0, 0.1)  # z, t0, x0 (-> |x0|), x1, c
+
+
+def with_oracle_flux(wl, seed=11, noiseless=False):
+    """Fill observed fluxes with oracle model values at the truth + 5% noise."""
+    o = oracle.Oracle(wl.model, wl.bands)
+    tb = W.truth_batch(wl.batch)
+    m = o.bandflux(tb)
+    W.add_noise(wl.batch, m, np.random.default_rng(seed), noiseless=noiseless)
+    return o
+
+
+def bf_scale(batch, ref):
+    """Per-bandflux comparison scale max(|B|, floor * max |B| over its SN)."""
+    scale = np.abs(ref).astype(np.float64)
+    off = oracle.Oracle.bandflux_offsets(batch)
+    for s in range(batch.n_sn):
+        lo, hi = off[s], off[s + 1]
+        if hi > lo:
+            scale[lo:hi] = np.maximum(scale[lo:hi], BF_FLOOR * np.abs(ref[lo:hi]).max())
+    return scale
+
+
+def assert_bandflux_close(batch, got, ref, rtol=BF_RTOL):
+    got = np.asarray(got, dtype=np.float64)
+    err = np.abs(got - ref) / np.maximum(bf_scale(batch, ref), 1e-300)
+    assert np.all(np.isfinite(got))
+    worst = float(err.max()) if err.size else 0.0
+    assert worst <= rtol, f"max relative bandflux error {worst:.3e} > {rtol}"
+    return worst
+
+
+def chi2_bound(batch, bf_ref, rtol=BF_RTOL):
+    """|dchi2| <= sum_i 2|r_i| e_i + e_i^2 with e_i = rtol * scale_i / sigma_i."""
+    off = oracle.Oracle.bandflux_offsets(batch)
+    scale = bf_scale(batch, bf_ref)
+    out = np.zeros(batch.n_par)
+    for s in range(batch.n_sn):
+        n = int(batch.obs_off[s + 1] - batch.obs_off[s])
+        if n == 0:
+            continue
+        f = batch.flux[batch.obs_off[s]:batch.obs_off[s + 1]].astype(np.float64)
+        sig = batch.fluxerr[batch.obs_off[s]:batch.obs_off[s + 1]].astype(np.float64)
+        for jj, j in enumerate(range(batch.par_off[s], batch.par_off[s + 1])):
+            sl = slice(off[s] + jj * n, off[s] + (jj + 1) * n)
+            r = (f - bf_ref[sl]) / sig
+            e = rtol * scale[sl] / sig
+            out[j] = np.sum(2 * np.abs(r) * e + e * e)
+    return out
+
+
+def assert_chi2_close(batch, got, ref, bf_ref):
+    got = np.asarray(got, dtype=np.float64)
+    bound = chi2_bound(batch, bf_ref) + 1e-12 * np.abs(ref) + 1e-12
+    err = np.abs(got - ref)
+    assert np.all(np.isfinite(got))
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"chi2 outside its bound at {bad[:5]}: {err[bad[:5]]} > {bound[bad[:5]]}"
+    return float(np.max(err / np.maximum(bound, 1e-300))) if err.size else 0.0
+
+
+def grad_scale(batch):
+    return np.stack([np.full(batch.n_par, SCALES[0]), np.full(batch.n_par, SCALES[1]),
+                     np.abs(batch.x0.astype(np.float64)), np.full(batch.n_par, SCALES[3]),
+                     np.full(batch.n_par, SCALES[4])], 1)
+
+
+def assert_grad_close(batch, got, ref, rtol=GRAD_RTOL):
+    s = grad_scale(batch)
+    gs = np.asarray(got, np.float64) * s
+    rs = np.asarray(ref, np.float64) * s
+    norm = np.max(np.abs(rs), axis=1, keepdims=True)
+    err = np.abs(gs - rs) / np.maximum(norm, 1e-300)
+    assert np.all(np.isfinite(gs))
+    worst = float(err.max()) if err.size else 0.0
+    assert worst <= rtol, f"max scaled gradient error {worst:.3e} > {rtol}"
+    return worst

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances: bandflux 1e-5 relative (floor 1e-3 of the supernova's largest
+bandflux); chi^2 within the bound that 1e-5 relative bandflux errors
+propagate to; gradient 1e-3 of the scaled gradient's inf-norm per sample."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests import _helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KERNELS = {"direct": 1, "factorised": 2}
+
+
+def _salt(wl, **kw):
+    from paper_2504_08081_b300 import build
+    build.build()
+    from paper_2504_08081_b300.torch_api import Salt
+    return Salt(wl.model, wl.bands, **kw)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    wl = W.config1()
+    o = H.with_oracle_flux(wl)
+    return wl, o
+
+
+@pytest.fixture(scope="module")
+def cfg2_sub():
+    wl = W.config2(n_sn=160)
+    o = H.with_oracle_flux(wl)
+    return wl, o
+
+
+@pytest.fixture(scope="module")
+def cfg3_sub():
+    wl = W.config3(n_sn=6, n_samples=40)
+    o = H.with_oracle_flux(wl)
+    return wl, o
+
+
+@pytest.fixture(scope="module")
+def cfg5_sub():
+    wl = W.config5(n_sn=60, n_samples=19)
+    o = H.with_oracle_flux(wl)
+    return wl, o
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_bandflux_single_supernova(cfg1, kernel):
+    wl, o = cfg1
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(wl.batch)
+    got = s.bandflux(db).cpu().numpy()
+    ref = o.bandflux(wl.batch)
+    H.assert_bandflux_close(wl.batch, got, ref)
+    s.check()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("tile", [1, 2, 4, 8])
+def test_bandflux_and_chi2_batched(cfg2_sub, kernel, tile):
+    wl, o = cfg2_sub
+    bt = wl.batch
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    s.set_tile(tile)
+    db = s.upload(bt)
+    bf = s.bandflux(db).cpu().numpy()
+    ref_bf = o.bandflux(bt)
+    H.assert_bandflux_close(bt, bf, ref_bf)
+    x2 = s.chi2(db).cpu().numpy()
+    H.assert_chi2_close(bt, x2, o.chi2(bt), ref_bf)
+    s.check()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("tile", [1, 4, 8])
+def test_chi2_grad_many_samples(cfg3_sub, kernel, tile):
+    wl, o = cfg3_sub
+    bt = wl.batch
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    s.set_tile(tile)
+    db = s.upload(bt)
+    x2, g = s.chi2_grad(db)
+    x2, g = x2.cpu().numpy(), g.cpu().numpy()
+    ref_x2, ref_g = o.chi2(bt, grad=True)
+    ref_bf = o.bandflux(bt)
+    H.assert_chi2_close(bt, x2, ref_x2, ref_bf)
+    H.assert_grad_close(bt, g, ref_g)
+    # the chi^2 of the gradient call agrees with the chi^2-only call (separately
+    # compiled variants: equal up to FP32 contraction order)
+    x2b = s.chi2(db).cpu().numpy()
+    H.assert_chi2_close(bt, x2b, ref_x2, ref_bf)
+    np.testing.assert_allclose(x2, x2b, rtol=1e-5)
+    s.check()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_large_grid_ragged(cfg5_sub, kernel):
+    wl, o = cfg5_sub
+    bt = wl.batch
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(bt)
+    bf = s.bandflux(db).cpu().numpy()
+    ref_bf = o.bandflux(bt)
+    H.assert_bandflux_close(bt, bf, ref_bf)
+    x2, g = s.chi2_grad(db)
+    ref_x2, ref_g = o.chi2(bt, grad=True)
+    H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    s.check()
+
+
+def test_factorised_matches_direct_kernel(cfg3_sub):
+    wl, o = cfg3_sub
+    s = _salt(wl)
+    db = s.upload(wl.batch)
+    s.set_kernel(1)
+    a = s.bandflux(db).cpu().numpy().astype(np.float64)
+    s.set_kernel(2)
+    b = s.bandflux(db).cpu().numpy().astype(np.float64)
+    H.assert_bandflux_close(wl.batch, b, a, rtol=2e-5)
+
+
+def test_bitwise_reproducible(cfg3_sub):
+    wl, _ = cfg3_sub
+    s = _salt(wl)
+    db = s.upload(wl.batch)
+    x2a, ga = s.chi2_grad(db)
+    outs = [s.chi2_grad(db) for _ in range(3)]
+    for x2, g in outs:
+        assert torch.equal(x2, x2a) and torch.equal(g, ga)
+    bfa = s.bandflux(db)
+    assert torch.equal(s.bandflux(db), bfa)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _edge_workload():
+    """Supernovae exercising the degenerate cases: no observations, no samples,
+    one observation, a 2-sample band, a band partly outside the grid at the
+    sample's z, phases outside the grid, samples at grid nodes and at the
+    colour-law boundaries."""
+    rng = np.random.default_rng(77)
+    model = W.make_model(rng)
+    bands = [W.gaussian_band(5500.0, 201), W.Band(wave=np.array([6000.0, 6400.0]),
+                                                  trans=np.array([0.7, 1.0])),
+             W.tophat_band(2900.0, 3300.0), W.gaussian_band(8600.0, 241),
+             W.tophat_band(6900.0, 7100.0, 2.5)]
+    n_obs = [0, 5, 1, 12, 7, 30]
+    n_par = [3, 0, 1, 4, 5, 9]
+    z = [0.05, 0.2, 0.004, 0.3, 0.1, 0.02]
+    bt = W.make_batch(rng, model, bands, n_obs, z, n_par, perturb=W.PERTURB)
+    # assign bands explicitly (all of them valid ids)
+    bt.band[:] = rng.integers(0, len(bands), size=bt.n_obs).astype(np.int32)
+    # supernova 3: phases beyond both ends of the grid for some observations
+    lo, hi = bt.obs_off[3], bt.obs_off[4]
+    bt.mjd[lo:lo + 3] = bt.t0[bt.par_off[3]] + np.array([-40.0, 80.0, 51.0 * 1.3])
+    # supernova 4: z = 0 sample, epochs on grid nodes, rest wavelength at the
+    # colour-law boundaries and at a grid node
+    p4 = bt.par_off[4]
+    bt.z[p4] = 0.0
+    lo = bt.obs_off[4]
+    bt.mjd[lo:lo + 3] = bt.t0[p4] + np.array([0.0, 7.0, -20.0])
+    bt.band[lo:lo + 3] = np.array([4, 4, 2], dtype=np.int32)
+    wl = W.Workload("edge", model, bands, bt)
+    return wl
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_edge_cases(kernel):
+    wl = _edge_workload()
+    o = H.with_oracle_flux(wl)
+    bt = wl.batch
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(bt)
+    ref_bf = o.bandflux(bt)
+    bf = s.bandflux(db).cpu().numpy()
+    H.assert_bandflux_close(bt, bf, ref_bf)
+    x2, g = s.chi2_grad(db)
+    ref_x2, ref_g = o.chi2(bt, grad=True)
+    H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    # supernova 0 has no observations: chi^2 = 0 and zero gradient exactly
+    p0 = slice(bt.par_off[0], bt.par_off[1])
+    assert np.all(x2.cpu().numpy()[p0] == 0.0) and np.all(g.cpu().numpy()[p0] == 0.0)
+    s.check()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_many_samples_one_supernova(kernel):
+    wl = W.config3(n_sn=1, n_samples=4096)
+    o = H.with_oracle_flux(wl)
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(wl.batch)
+    x2, g = s.chi2_grad(db)
+    idx = np.random.default_rng(3).choice(4096, 64, replace=False)
+    sub = W.Batch(obs_off=wl.batch.obs_off, mjd=wl.batch.mjd, band=wl.batch.band,
+                  flux=wl.batch.flux, fluxerr=wl.batch.fluxerr, zp=wl.batch.zp,
+                  par_off=np.array([0, len(idx)], dtype=np.int64), t0=wl.batch.t0[idx],
+                  z=wl.batch.z[idx], x0=wl.batch.x0[idx], x1=wl.batch.x1[idx], c=wl.batch.c[idx])
+    ref_x2, ref_g = o.chi2(sub, grad=True)
+    H.assert_chi2_close(sub, x2.cpu().numpy()[idx], ref_x2, o.bandflux(sub))
+    H.assert_grad_close(sub, g.cpu().numpy()[idx], ref_g)
+
+
+def test_invalid_data_is_reported():
+    from paper_2504_08081_b300 import SaltError
+    wl = W.config2(n_sn=5)
+    H.with_oracle_flux(wl)
+    s = _salt(wl)
+    bt = wl.batch
+    bt.band = bt.band.copy()
+    bt.band[3] = 17  # out of range
+    db = s.upload(bt)
+    with pytest.raises(SaltError) as ei:
+        s.chi2(db, validate=True)
+    assert ei.value.code == -1
+    x2 = s.chi2(db).cpu().numpy()
+    assert np.isnan(x2[0]) and np.all(np.isfinite(x2[1:]))
+    with pytest.raises(SaltError) as ei:
+        s.check()
+    assert ei.value.code == -7
+    s.check()  # the sticky flag was cleared
+
+
+def test_autograd_function(cfg3_sub):
+    from paper_2504_08081_b300.torch_api import SaltChi2
+    wl, o = cfg3_sub
+    s = _salt(wl)
+    db = s.upload(wl.batch)
+    z = db.t["z"].clone().requires_grad_(True)
+    t0 = db.t["t0"].clone().requires_grad_(True)
+    x0 = db.t["x0"].clone().requires_grad_(True)
+    x1 = db.t["x1"].clone().requires_grad_(True)
+    c = db.t["c"].clone().requires_grad_(True)
+    x2 = SaltChi2.apply(s, db, z, t0, x0, x1, c)
+    w = torch.linspace(0.5, 1.5, x2.numel(), device=x2.device, dtype=x2.dtype)
+    (x2 * w).sum().backward()
+    _, g = s.chi2_grad(db)
+    wf = w.float()[:, None]
+    for q, t in enumerate((z, t0, x0, x1, c)):
+        torch.testing.assert_close(t.grad.float(), (g * wf)[:, q], rtol=1e-6, atol=0)
+
+
+def test_gradient_against_central_differences_on_gpu(cfg3_sub):
+    # the GPU adjoint against GPU central differences of the GPU chi^2 for the
+    # parameters chi^2 is smooth in (x0, x1 enter quadratically, c smoothly);
+    # a looser check than the oracle comparison
+    wl, _ = cfg3_sub
+    s = _salt(wl)
+    db = s.upload(wl.batch)
+    _, g = s.chi2_grad(db)
+    g = g.cpu().numpy().astype(np.float64)
+    for q, name in ((2, "x0"), (3, "x1"), (4, "c")):
+        base = db.t[name]
+        h = {"x0": 1e-2 * base.abs(), "x1": torch.full_like(base, 1e-2),
+             "c": torch.full_like(base, 1e-3)}[name]
+        up, dn = base + h, base - h
+        xp = s.chi2(db.with_params(**{name: up})).double()
+        xm = s.chi2(db.with_params(**{name: dn})).double()
+        fd = ((xp - xm) / (up.double() - dn.double())).cpu().numpy()
+        scale = np.abs(g[:, q]) + 1e-2 * np.abs(g[:, q]).max() + 1e-300
+        assert np.median(np.abs(fd - g[:, q]) / scale) < 1e-2, name
