@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5])
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle CPU-baseline budget")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed steps only (no e2e, CPU baseline or secondary workloads): for ncu")
     return ap.parse_args()
 
 
@@ -318,6 +320,13 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         salt.check()
     ms = statistics.mean(durs)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": W.CONFIG_NAMES[args.workload], "ms_per_step": ms,
+                              "bandfluxes": bt.n_bandflux()}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
     nbf_t = torch.tensor([float(bt.n_bandflux()), float(bt.n_par)], dtype=torch.float64, device=dev)
     if world > 1:

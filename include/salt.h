@@ -133,10 +133,15 @@ typedef struct {
     int32_t validate;
 } salt_batch;
 
-/* Precompute the launch plan for a batch layout (host CSR offsets): the
- * cost-sorted work list of (supernova, sample-tile) items, the device copies
- * of the offsets and the tile choice. Reusable for every batch with the same
- * offsets (the parameters and observation values may change between calls). */
+/* Precompute the launch plan for a batch layout (host CSR offsets): device
+ * copies of the offsets and, on first use, the cost-sorted work lists of
+ * (supernova, sample-range) items. Reusable for every batch with the same
+ * offsets (parameters and observation values may change between calls).
+ * With SALT_KERNEL_AUTO the first batch call of each mode on a plan
+ * autotunes: it times every candidate kernel family / tile on that batch,
+ * synchronising the stream, and keeps the fastest (cached per layout for the
+ * process, and appended to the file named by SALT_TUNE_CACHE if set). A plan
+ * must not be used from two threads at once. */
 int salt_plan_create(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,
                      salt_plan **out);
 void salt_plan_destroy(salt_plan *plan);
@@ -169,15 +174,16 @@ int salt_check(salt_ctx *ctx, void *cuda_stream);
 
 typedef enum {
     SALT_OPT_KERNEL = 1,       /* SALT_KERNEL_* : which kernel family batch calls use */
-    SALT_OPT_TILE_SAMPLES = 2, /* samples per work item (0 = autotuned / default) */
+    SALT_OPT_TILE_SAMPLES = 2, /* samples per tile for the forced kernel families (0 = default) */
     SALT_OPT_GRAPHS = 3,       /* 1 = replay batch calls from captured CUDA graphs (default 1) */
     SALT_OPT_SERVE_CHUNK = 4   /* serving: samples per chunk (default 64) */
 } salt_option;
 
 typedef enum {
-    SALT_KERNEL_AUTO = 0,        /* factorised fused kernel */
+    SALT_KERNEL_AUTO = 0,        /* factorised path; family and tile autotuned per plan and mode */
     SALT_KERNEL_DIRECT = 1,      /* per-band-sample evaluation straight from Eq. 1-2 */
-    SALT_KERNEL_FACTORISED = 2   /* per-(sample, band) column response, shared by observations */
+    SALT_KERNEL_FACTORISED = 2,  /* factorised, CTA-cooperative per (sample tile, band) */
+    SALT_KERNEL_BANDWARP = 3     /* factorised, one warp per (band, 1-2 samples); <= 128 phase nodes */
 } salt_kernel;
 
 int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value);

@@ -214,22 +214,16 @@ static bool offsets_ok(int64_t n_sn, const int64_t *off) {
     return true;
 }
 
-static int default_tile(const salt_ctx *ctx, int64_t n_sn, int64_t n_par) {
-    if (ctx->tile_samples > 0) return ctx->tile_samples;
-    const double mean = n_sn > 0 ? (double)n_par / (double)n_sn : 1.0;
-    if (mean >= 8) return 8;
-    if (mean >= 4) return 4;
-    if (mean >= 2) return 2;
-    return 1;
-}
-
-int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off, int tile,
+int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off, int /*tile*/,
                salt_plan *p, cudaStream_t st, bool async_alloc) {
     if (n_sn < 0 || !offsets_ok(n_sn, obs_off) || !offsets_ok(n_sn, par_off))
         return set_err(ctx, SALT_ERR_INVALID, "offsets must start at 0 and be nondecreasing");
-    for (int64_t s = 0; s < n_sn; ++s)
+    for (int64_t s = 0; s < n_sn; ++s) {
         if (par_off[s + 1] - par_off[s] > INT32_MAX / 2)
             return set_err(ctx, SALT_ERR_INVALID, "too many samples for one supernova");
+        if (obs_off[s + 1] - obs_off[s] > INT32_MAX / 2)
+            return set_err(ctx, SALT_ERR_INVALID, "too many observations for one supernova");
+    }
     p->ctx = ctx;
     p->device = ctx->device;
     p->n_sn = n_sn;
@@ -241,35 +235,6 @@ int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_
     for (int64_t s = 0; s < n_sn; ++s)
         p->bf_off_h[s + 1] = p->bf_off_h[s] + (obs_off[s + 1] - obs_off[s]) * (par_off[s + 1] - par_off[s]);
     p->n_bandflux = p->bf_off_h[n_sn];
-    if (tile <= 0) tile = default_tile(ctx, n_sn, p->n_par);
-    if (tile != 1 && tile != 2 && tile != 4 && tile != 8) tile = 8;
-    p->tile = tile;
-    // tiles per item: enough items to keep every SM busy and balanced
-    int64_t total_tiles = 0;
-    for (int64_t s = 0; s < n_sn; ++s) total_tiles += (par_off[s + 1] - par_off[s] + tile - 1) / tile;
-    int64_t target = (int64_t)ctx->num_sms * 16;
-    int tpi = (int)std::min<int64_t>(8, std::max<int64_t>(1, total_tiles / std::max<int64_t>(target, 1)));
-    p->tiles_per_item = tpi;
-    struct Cost { double c; WorkItem w; };
-    std::vector<Cost> items;
-    items.reserve((size_t)(total_tiles / tpi + n_sn + 1));
-    const int span = tile * tpi;
-    for (int64_t s = 0; s < n_sn; ++s) {
-        const int64_t S = par_off[s + 1] - par_off[s];
-        const int64_t n = obs_off[s + 1] - obs_off[s];
-        for (int64_t j0 = 0; j0 < S; j0 += span) {
-            const int nj = (int)std::min<int64_t>(span, S - j0);
-            const double cost = (double)((nj + tile - 1) / tile) * (64.0 + (double)n) * tile;
-            if (n > INT32_MAX) return set_err(ctx, SALT_ERR_INVALID, "too many observations for one supernova");
-            items.push_back({cost, WorkItem{obs_off[s], par_off[s] + j0, p->bf_off_h[s], (int32_t)n, nj,
-                                            (int32_t)j0, 0}});
-        }
-    }
-    std::stable_sort(items.begin(), items.end(), [](const Cost &x, const Cost &y) { return x.c > y.c; });
-    std::vector<WorkItem> wl(items.size());
-    for (size_t q = 0; q < items.size(); ++q) wl[q] = items[q].w;
-    p->n_items = (int)wl.size();
-    // device copies
     auto alloc = [&](void **ptr, size_t bytes) -> cudaError_t {
         bytes = std::max<size_t>(bytes, 16);
         return async_alloc ? cudaMallocAsync(ptr, bytes, st) : cudaMalloc(ptr, bytes);
@@ -277,17 +242,58 @@ int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_
     CK(alloc((void **)&p->obs_off_d, (n_sn + 1) * 8), "alloc offsets");
     CK(alloc((void **)&p->par_off_d, (n_sn + 1) * 8), "alloc offsets");
     CK(alloc((void **)&p->bf_off_d, (n_sn + 1) * 8), "alloc offsets");
-    CK(alloc((void **)&p->items_d, wl.size() * sizeof(WorkItem)), "alloc work list");
     CK(alloc((void **)&p->counter_d, 16), "alloc counter");
     CK(cudaMemcpyAsync(p->obs_off_d, obs_off, (n_sn + 1) * 8, cudaMemcpyHostToDevice, st), "upload offsets");
     CK(cudaMemcpyAsync(p->par_off_d, par_off, (n_sn + 1) * 8, cudaMemcpyHostToDevice, st), "upload offsets");
     CK(cudaMemcpyAsync(p->bf_off_d, p->bf_off_h.data(), (n_sn + 1) * 8, cudaMemcpyHostToDevice, st),
        "upload offsets");
-    if (!wl.empty())
-        CK(cudaMemcpyAsync(p->items_d, wl.data(), wl.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
-           "upload work list");
-    // pageable sources: the copies above complete before return when not async
     if (async_alloc) CK(cudaStreamSynchronize(st), "plan upload");
+    return SALT_OK;
+}
+
+// Work list for one launch configuration: (supernova, sample-range) items,
+// longest first (cost ~ tiles x (observations + per-band setup)).
+static int build_items(salt_ctx *ctx, salt_plan *p, int key, cudaStream_t st) {
+    if (p->lists.count(key)) return SALT_OK;
+    const int family = cfg_family(key), tile = cfg_tile(key);
+    const int64_t n_sn = p->n_sn;
+    const int64_t *po = p->par_off_h.data(), *oo = p->obs_off_h.data();
+    int span;
+    if (family == FAM_WARP) {
+        span = bandwarp_item_samples();
+    } else {
+        int64_t total_tiles = 0;
+        for (int64_t s = 0; s < n_sn; ++s) total_tiles += (po[s + 1] - po[s] + tile - 1) / tile;
+        const int64_t target = (int64_t)ctx->num_sms * 16;
+        const int tpi = (int)std::min<int64_t>(8, std::max<int64_t>(1, total_tiles / std::max<int64_t>(target, 1)));
+        span = tile * tpi;
+    }
+    struct Cost { double c; WorkItem w; };
+    std::vector<Cost> items;
+    for (int64_t s = 0; s < n_sn; ++s) {
+        const int64_t S = po[s + 1] - po[s];
+        const int64_t n = oo[s + 1] - oo[s];
+        for (int64_t j0 = 0; j0 < S; j0 += span) {
+            const int nj = (int)std::min<int64_t>(span, S - j0);
+            const double cost = (double)((nj + tile - 1) / tile) * (64.0 + (double)n) * tile;
+            items.push_back({cost, WorkItem{oo[s], po[s] + j0, p->bf_off_h[s], (int32_t)n, nj, (int32_t)j0, 0}});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Cost &x, const Cost &y) { return x.c > y.c; });
+    std::vector<WorkItem> wl(items.size());
+    for (size_t q = 0; q < items.size(); ++q) wl[q] = items[q].w;
+    salt_plan::ItemList L;
+    L.n = (int)wl.size();
+    const size_t bytes = std::max<size_t>(wl.size() * sizeof(WorkItem), 16);
+    CK(p->temporary ? cudaMallocAsync((void **)&L.d, bytes, st) : cudaMalloc((void **)&L.d, bytes),
+       "alloc work list");
+    p->lists[key] = L;
+    if (!wl.empty()) {
+        CK(cudaMemcpyAsync(L.d, wl.data(), wl.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
+           "upload work list");
+        // pageable source: staged before return, but keep the host copy alive until then
+        CK(cudaStreamSynchronize(st), "upload work list");
+    }
     return SALT_OK;
 }
 
@@ -295,23 +301,161 @@ void plan_free(salt_plan *p, cudaStream_t st) {
     for (auto &kv : p->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     p->graphs.clear();
-    void *ptrs[] = {p->obs_off_d, p->par_off_d, p->bf_off_d, p->items_d, p->counter_d};
+    std::vector<void *> ptrs = {p->obs_off_d, p->par_off_d, p->bf_off_d, p->counter_d};
+    for (auto &kv : p->lists) ptrs.push_back(kv.second.d);
     for (void *q : ptrs)
         if (q) {
             if (p->temporary) cudaFreeAsync(q, st); else cudaFree(q);
         }
+    p->lists.clear();
     p->obs_off_d = p->par_off_d = p->bf_off_d = nullptr;
-    p->items_d = nullptr;
     p->counter_d = nullptr;
 }
 
-int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *plan, const OutDev &o, int mode,
+static cudaError_t launch_key(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b, const OutDev &o, int mode,
+                              cudaStream_t st) {
+    const salt_plan::ItemList &L = p->lists[key];
+    if (cfg_family(key) == FAM_WARP)
+        return launch_bandwarp_items(ctx, cfg_tile(key), L.d, L.n, p->counter_d, b, o, mode, st);
+    return launch_factorised_items(ctx, cfg_tile(key), L.d, L.n, p->counter_d, b, o, mode, st);
+}
+
+// Heuristic configuration (used for one-off plans and while capturing).
+static int default_config(const salt_ctx *ctx, const salt_plan *p) {
+    const double mean = p->n_sn > 0 ? (double)p->n_par / (double)p->n_sn : 1.0;
+    const bool warp_ok = ctx->mp.n_phase <= bandwarp_max_phase();
+    if (warp_ok && mean < 4) return cfg_key(FAM_WARP, mean >= 2 ? 2 : 1);
+    if (mean >= 8) return cfg_key(FAM_CTA, 8);
+    if (mean >= 4) return cfg_key(FAM_CTA, 4);
+    return cfg_key(FAM_CTA, mean >= 2 ? 2 : 1);
+}
+
+// Autotuner: process-wide cache of tuned configurations keyed by the batch
+// layout signature, optionally persisted as JSON lines (SALT_TUNE_CACHE).
+struct TuneCache {
+    std::mutex mu;
+    std::map<std::string, int> best;
+    bool loaded = false;
+    void load() {
+        if (loaded) return;
+        loaded = true;
+        const char *path = getenv("SALT_TUNE_CACHE");
+        if (!path) return;
+        FILE *f = fopen(path, "r");
+        if (!f) return;
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+            char sig[400];
+            int key;
+            if (sscanf(line, "{\"sig\": \"%399[^\"]\", \"key\": %d}", sig, &key) == 2) best[sig] = key;
+        }
+        fclose(f);
+    }
+    void store(const std::string &sig, int key) {
+        best[sig] = key;
+        const char *path = getenv("SALT_TUNE_CACHE");
+        if (!path) return;
+        FILE *f = fopen(path, "a");
+        if (!f) return;
+        fprintf(f, "{\"sig\": \"%s\", \"key\": %d}\n", sig.c_str(), key);
+        fclose(f);
+    }
+};
+static TuneCache g_tune;
+
+static std::string plan_signature(const salt_ctx *ctx, const salt_plan *p, int mode) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "sm%d np%d nw%d nb%d m%d sn%lld obs%lld par%lld", ctx->num_sms, ctx->mp.n_phase,
+             ctx->mp.n_wave, ctx->mp.bands.n_bands, mode, (long long)p->n_sn, (long long)p->n_obs,
+             (long long)p->n_par);
+    return buf;
+}
+
+static int tune(salt_ctx *ctx, salt_plan *p, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st,
+                int *best_key) {
+    std::vector<int> cands;
+    const double mean = p->n_sn > 0 ? (double)p->n_par / (double)p->n_sn : 1.0;
+    for (int t : {1, 2, 4, 8})
+        if (t == 1 || mean >= 0.75 * t) cands.push_back(cfg_key(FAM_CTA, t));
+    if (ctx->mp.n_phase <= bandwarp_max_phase()) {
+        cands.push_back(cfg_key(FAM_WARP, 1));
+        if (mean >= 1.5) cands.push_back(cfg_key(FAM_WARP, 2));
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "tune");
+    CK(cudaEventCreate(&e1), "tune");
+    float best_ms = 1e30f;
+    int best = -1;
+    int rc = SALT_OK;
+    for (int key : cands) {
+        if ((rc = build_items(ctx, p, key, st)) != SALT_OK) break;
+        cudaError_t e = launch_key(ctx, p, key, b, o, mode, st);  // warm
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_key(ctx, p, key, b, o, mode, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess) ms = std::min(ms, t);
+        }
+        if (e != cudaSuccess) { rc = cuda_err(ctx, e, "autotune"); break; }
+        if (ms < best_ms) { best_ms = ms; best = key; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SALT_OK) return rc;
+    *best_key = best;
+    return SALT_OK;
+}
+
+int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const OutDev &o, int mode,
               cudaStream_t st) {
-    cudaError_t e;
-    if (ctx->kernel == SALT_KERNEL_DIRECT)
-        e = launch_direct(ctx, b, o, mode, st);
-    else
-        e = launch_factorised(ctx, plan, b, o, mode, st);
+    salt_plan *p = const_cast<salt_plan *>(cplan);  // tuning state and work lists are a cache
+    if (ctx->kernel == SALT_KERNEL_DIRECT) {
+        cudaError_t e = launch_direct(ctx, b, o, mode, st);
+        return e == cudaSuccess ? SALT_OK : cuda_err(ctx, e, "kernel launch");
+    }
+    int key = 0;
+    const int tile = ctx->tile_samples;
+    if (ctx->kernel == SALT_KERNEL_FACTORISED) {
+        key = cfg_key(FAM_CTA, tile > 0 ? tile : cfg_tile(default_config(ctx, p)));
+    } else if (ctx->kernel == SALT_KERNEL_BANDWARP) {
+        if (ctx->mp.n_phase > bandwarp_max_phase())
+            return set_err(ctx, SALT_ERR_INVALID, "band-warp kernel supports at most 128 phase nodes");
+        key = cfg_key(FAM_WARP, tile == 2 ? 2 : 1);
+    } else if (p->choice[mode] >= 0) {
+        key = p->choice[mode];
+    } else {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (p->temporary || cs != cudaStreamCaptureStatusNone) {
+            key = default_config(ctx, p);
+        } else {
+            const std::string sig = plan_signature(ctx, p, mode);
+            std::lock_guard<std::mutex> lk(g_tune.mu);
+            g_tune.load();
+            auto it = g_tune.best.find(sig);
+            if (it != g_tune.best.end()) {
+                key = it->second;
+            } else {
+                int rc = tune(ctx, p, b, o, mode, st, &key);
+                if (rc != SALT_OK) return rc;
+                g_tune.store(sig, key);
+            }
+            p->choice[mode] = key;
+        }
+    }
+    if (!p->lists.count(key)) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs != cudaStreamCaptureStatusNone)
+            return set_err(ctx, SALT_ERR_INVALID, "run a plan once outside stream capture before capturing it");
+    }
+    int rc = build_items(ctx, p, key, st);
+    if (rc != SALT_OK) return rc;
+    cudaError_t e = launch_key(ctx, p, key, b, o, mode, st);
     if (e != cudaSuccess) return cuda_err(ctx, e, "kernel launch");
     return SALT_OK;
 }
@@ -456,7 +600,7 @@ extern "C" int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value) {
     if (!ctx) return SALT_ERR_INVALID;
     switch (option) {
         case SALT_OPT_KERNEL:
-            if (value < 0 || value > 2) return SALT_ERR_INVALID;
+            if (value < 0 || value > 3) return SALT_ERR_INVALID;
             ctx->kernel = (int)value;
             return SALT_OK;
         case SALT_OPT_TILE_SAMPLES:

@@ -1,0 +1,567 @@
+// Band-parallel factorised kernel: the same factorisation as k_fact (column
+// response E, row dots D = G E over touched phase rows, per-pair epilogue,
+// reverse-mode adjoint), but each warp owns one (band, group of TS samples)
+// unit and runs it warp-synchronously. A CTA takes one (supernova,
+// sample-range) item, spreads its units over 8 warps, and after a single
+// barrier reduces the per-(sample, band) partials in band order, so results
+// are bitwise reproducible for a given TS. Suited to items with few samples
+// (batched one-vector fits, small serving requests), where band-serial phases
+// separated by CTA barriers would leave most warps idle.
+#include "fact_common.cuh"
+
+namespace salt {
+namespace bw {
+
+constexpr int THREADS = 256;
+constexpr int WARPS = THREADS / 32;
+constexpr int OBS_MAX = 1024;  // observations of one supernova staged per pass
+constexpr int WMAXW = 192;     // window columns per chunk (per warp)
+constexpr int NPHW = 128;      // phase nodes supported by this kernel
+constexpr int NJ_MAX = 16;     // samples per item
+constexpr int NSLOT = 8;       // doubles per (sample, band) partial: chi2, g[6]
+
+using fk::al16;
+
+struct Lay {
+    size_t ord, zpf, bst, pj, t0, slots, misc, warp0, warp_bytes, total;
+    __host__ __device__ Lay(int ts, bool grad, int nb) {
+        const int ne = grad ? 3 : 1;
+        size_t o = 0;
+        ord = o;   o = al16(o + 4 * OBS_MAX);
+        zpf = o;   o = al16(o + 4 * OBS_MAX);
+        bst = o;   o = al16(o + 4 * (2 * SALT_MAX_BANDS + 2));
+        pj = o;    o = al16(o + 4 * 8 * NJ_MAX);
+        t0 = o;    o = al16(o + 8 * NJ_MAX);
+        slots = o; o = al16(o + 8 * (size_t)NSLOT * NJ_MAX * (nb > 0 ? nb : 1));
+        misc = o;  o = al16(o + 4 * (16 + SALT_MAX_BANDS));
+        warp0 = o;
+        // per warp: E [ne][WMAXW][ts], D [NPHW][ts][2], Y [NPHW][ts], rows [NPHW],
+        // kc[32], F[FSPAN+2], kw[32][4 ne], ykey[32], yval[32]
+        warp_bytes = al16(4 * (size_t)ne * WMAXW * ts) + al16(4 * (size_t)NPHW * ts * 2) +
+                     al16(grad ? 4 * (size_t)NPHW * ts : 0) + al16(4 * NPHW) +
+                     al16(4 * 32 + 4 * (fk::FSPAN + 2) + 4 * 32 * 4 * ne + 8 * 32);
+        o += WARPS * warp_bytes;
+        total = o;
+    }
+};
+
+enum { PJ_A = 0, PJ_X0, PJ_X1, PJ_C, PJ_OK };
+
+template <int TS, int MODE>
+__global__ void __launch_bounds__(THREADS, 2)
+k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items,
+           int *counter) {
+    constexpr bool GRAD = MODE == MODE_GRAD;
+    constexpr int NE = GRAD ? 3 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NB = m.bands.n_bands;
+    const Lay L(TS, GRAD, NB);
+    int *sOrd = (int *)(smem + L.ord);
+    float *sZpf = (float *)(smem + L.zpf);
+    int *sBst = (int *)(smem + L.bst);
+    float *sPj = (float *)(smem + L.pj);  // [5][NJ_MAX]
+    double *sT0 = (double *)(smem + L.t0);
+    double *sSlot = (double *)(smem + L.slots);  // [NJ_MAX][NB][NSLOT]
+    int *sMisc = (int *)(smem + L.misc);
+    int *sPresent = sMisc + 16;  // present band ids, in band order
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NW = m.n_wave, NP = m.n_phase;
+
+    unsigned char *wbase = smem + L.warp0 + (size_t)warp * L.warp_bytes;
+    float *E = (float *)wbase;  // [NE][WMAXW][TS]
+    float *D = (float *)(wbase + al16(4 * (size_t)NE * WMAXW * TS));  // [NPHW][TS][2]
+    float *Y = (float *)((unsigned char *)D + al16(4 * (size_t)NPHW * TS * 2));  // [NPHW][TS]
+    int *rowl = (int *)((unsigned char *)Y + al16(GRAD ? 4 * (size_t)NPHW * TS : 0));
+    int *kc = (int *)((unsigned char *)rowl + al16(4 * NPHW));
+    int *F = kc + 32;
+    float *kw = (float *)(F + fk::FSPAN + 2);
+    int *ykey = (int *)(kw + 32 * 4 * NE);
+    float *yval = (float *)(ykey + 32);
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sMisc[0] = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = sMisc[0];
+        if (it >= n_items) break;
+        const WorkItem wi = items[it];
+        const int64_t ob0 = wi.obs0;
+        const int64_t nobs = wi.nobs;
+        const int nj = wi.nj;  // <= NJ_MAX
+
+        if (tid < NJ_MAX) {
+            const int j = tid;
+            float z = 0.f, x0 = 0.f, x1 = 0.f, c = 0.f;
+            double t0 = 0.0;
+            int ok = 0;
+            if (j < nj) {
+                const int64_t g = wi.par0 + j;
+                z = b.z[g]; x0 = b.x0[g]; x1 = b.x1[g]; c = b.c[g]; t0 = b.t0[g];
+                ok = isfinite(z) && z > -1.f && isfinite(x0) && isfinite(x1) && isfinite(c) && isfinite(t0);
+                if (!ok) atomicOr(o.err, ERRBIT_PARAM);
+            }
+            if (!ok) { z = 0.f; x0 = 0.f; x1 = 0.f; c = 0.f; t0 = 0.0; }
+            sPj[PJ_A * NJ_MAX + j] = 1.0f / (1.0f + z);
+            sPj[PJ_X0 * NJ_MAX + j] = x0;
+            sPj[PJ_X1 * NJ_MAX + j] = x1;
+            sPj[PJ_C * NJ_MAX + j] = c;
+            sPj[PJ_OK * NJ_MAX + j] = (j < nj && ok) ? 1.f : 0.f;
+            sT0[j] = t0;
+        }
+        if (tid == 0) sMisc[2] = 0;
+        for (int q = tid; q < NSLOT * NJ_MAX * NB; q += THREADS) sSlot[q] = 0.0;
+
+        for (int64_t oc = 0; oc < nobs; oc += OBS_MAX) {
+            const int nc = (int)min((int64_t)OBS_MAX, nobs - oc);
+            const int64_t obase = ob0 + oc;
+            __syncthreads();
+            for (int i = tid; i < 2 * SALT_MAX_BANDS + 2; i += THREADS) sBst[i] = 0;
+            __syncthreads();
+            for (int i = tid; i < nc; i += THREADS) {
+                const int bd = b.band[obase + i];
+                const float e = b.fluxerr[obase + i];
+                const bool okb = bd >= 0 && bd < NB;
+                if (!okb || !(e > 0.f)) {
+                    atomicOr(o.err, okb ? ERRBIT_SIGMA : ERRBIT_BAND);
+                    sMisc[2] = 1;
+                }
+                sZpf[i] = zp_scale(b.zp[obase + i]);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int *cnt = sBst + 1;
+                for (int base = 0; base < nc; base += 32) {
+                    const int i = base + lane;
+                    int bd = -1;
+                    if (i < nc) {
+                        bd = b.band[obase + i];
+                        if (bd < 0 || bd >= NB || !(b.fluxerr[obase + i] > 0.f)) bd = -1;
+                    }
+                    const unsigned mm = __match_any_sync(0xffffffffu, bd);
+                    if (bd >= 0 && lane == __ffs(mm) - 1) cnt[bd] += __popc(mm);
+                    __syncwarp();
+                }
+                if (lane == 0) {
+                    int acc = 0, np = 0;
+                    for (int q = 0; q <= NB; ++q) {
+                        const int v = (q < NB) ? sBst[q + 1] : 0;
+                        sBst[q] = acc;
+                        sBst[NB + 1 + q] = acc;
+                        if (q < NB && v > 0) sPresent[np++] = q;
+                        acc += v;
+                    }
+                    sMisc[3] = np;
+                }
+                __syncwarp();
+                int *pos = sBst + NB + 1;
+                for (int base = 0; base < nc; base += 32) {
+                    const int i = base + lane;
+                    int bd = -1;
+                    if (i < nc) {
+                        bd = b.band[obase + i];
+                        if (bd < 0 || bd >= NB || !(b.fluxerr[obase + i] > 0.f)) bd = -1;
+                    }
+                    const unsigned mm = __match_any_sync(0xffffffffu, bd);
+                    const int rank = __popc(mm & ((1u << lane) - 1u));
+                    if (bd >= 0) sOrd[pos[bd] + rank] = i;
+                    __syncwarp();
+                    if (bd >= 0 && lane == __ffs(mm) - 1) pos[bd] += __popc(mm);
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+
+            // ---- units: (present band, group of TS samples), round-robin over warps
+            const int npres = sMisc[3];
+            const int ngroups = (nj + TS - 1) / TS;
+            const int nunits = npres * ngroups;
+            for (int u = warp; u < nunits; u += WARPS) {
+                const int bi = u / ngroups, grp = u - bi * ngroups;
+                const int bd = sPresent[bi];
+                const int j0 = grp * TS;
+                const int ns = min(TS, nj - j0);
+                const int nb_obs = sBst[bd + 1] - sBst[bd];
+                const int *ordb = sOrd + sBst[bd];
+                const int K = m.bands.n[bd], koff = m.bands.off[bd];
+                const float *lam = m.band_lam + koff;
+                const float *wk = m.band_w + koff;
+
+                // 1. in-grid band-sample range per sample (contiguous in k) and union window
+                int kf[TS], kl[TS];
+                int clo = 0x7fffffff, chi = -1;
+#pragma unroll
+                for (int s = 0; s < TS; ++s) {
+                    kf[s] = K; kl[s] = -1;
+                    if (s < ns && sPj[PJ_OK * NJ_MAX + j0 + s] != 0.f) {
+                        const float a = sPj[PJ_A * NJ_MAX + j0 + s];
+                        for (int k0 = 0; k0 < K; k0 += 32) {
+                            const int k = k0 + lane;
+                            bool in = false;
+                            if (k < K) {
+                                const float lr = __ldg(lam + k) * a;
+                                in = lr >= m.wave0 && lr <= m.wave_max;
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, in);
+                            if (bal) {
+                                if (kf[s] == K) kf[s] = k0 + __ffs(bal) - 1;
+                                kl[s] = k0 + 31 - __clz(bal);
+                            }
+                        }
+                        if (kf[s] <= kl[s]) {
+                            int iv; float t;
+                            axis_locate(__ldg(lam + kf[s]) * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            clo = min(clo, fk::first_tap(iv, NW));
+                            axis_locate(__ldg(lam + kl[s]) * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            chi = max(chi, fk::first_tap(iv, NW) + 3);
+                        }
+                    }
+                }
+                // 2. touched phase rows (OR over lanes), compacted into rowl
+                unsigned msk[NPHW / 32] = {0u, 0u, 0u, 0u};
+                for (int base = 0; base < nb_obs; base += 32) {
+                    const int il = base + lane;
+                    if (il < nb_obs) {
+                        const int i = ordb[il];
+                        const double mj = b.mjd[obase + i];
+#pragma unroll
+                        for (int s = 0; s < TS; ++s) {
+                            if (s >= ns || sPj[PJ_OK * NJ_MAX + j0 + s] == 0.f) continue;
+                            const float p = (float)(mj - sT0[j0 + s]) * sPj[PJ_A * NJ_MAX + j0 + s];
+                            int iv; float t;
+                            if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
+                                const int first = fk::first_tap(iv, NP);
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) msk[(first + q) >> 5] |= 1u << ((first + q) & 31);
+                            }
+                        }
+                    }
+                }
+                int nrows = 0;
+#pragma unroll
+                for (int w = 0; w < NPHW / 32; ++w) {
+                    const unsigned word = __reduce_or_sync(0xffffffffu, msk[w]);
+                    const bool on = (word >> lane) & 1u;
+                    if (on) rowl[nrows + __popc(word & ((1u << lane) - 1u))] = w * 32 + lane;
+                    nrows += __popc(word);
+                }
+                __syncwarp();
+                for (int q = lane; q < nrows * TS * 2; q += 32) {
+                    const int rr = q / (TS * 2);
+                    D[rowl[rr] * TS * 2 + (q - rr * TS * 2)] = 0.f;
+                }
+                if (GRAD)
+                    for (int q = lane; q < nrows * TS; q += 32) Y[rowl[q / TS] * TS + (q % TS)] = 0.f;
+                __syncwarp();
+                const int nch = (chi >= clo) ? (chi - clo + WMAXW) / WMAXW : 0;
+                const bool one = nch == 1;
+
+                // 3. column response and forward row dots, per column chunk
+                for (int ch = 0; ch < nch; ++ch) {
+                    const int cc = clo + ch * WMAXW;
+                    const int W = min(WMAXW, chi - cc + 1);
+                    const int nez = (GRAD && one) ? NE : 1;
+                    for (int q = lane; q < nez * WMAXW * TS; q += 32) E[q] = 0.f;
+                    __syncwarp();
+#pragma unroll
+                    for (int s = 0; s < TS; ++s) {
+                        if (s >= ns || kf[s] > kl[s]) continue;
+                        const float a = sPj[PJ_A * NJ_MAX + j0 + s], c = sPj[PJ_C * NJ_MAX + j0 + s];
+                        if (GRAD && one)
+                            fk::ebuild<3, true>(m, lam, wk, kf[s], kl[s], kf[s], 32, a, c, cc, W, lane, kc, F, kw,
+                                                E + s, E + WMAXW * TS + s, E + 2 * WMAXW * TS + s, TS);
+                        else
+                            fk::ebuild<1, true>(m, lam, wk, kf[s], kl[s], kf[s], 32, a, c, cc, W, lane, kc, F, kw,
+                                                E + s, nullptr, nullptr, TS);
+                    }
+                    __syncwarp();
+                    // 4 lanes per row, 8 rows per pass, 4 columns in flight per lane
+                    const int l4 = lane & 3;
+                    for (int rb = 0; rb < nrows; rb += 8) {
+                        const int rr = rb + (lane >> 2);
+                        const bool valid = rr < nrows;
+                        const int r = valid ? rowl[rr] : 0;
+                        float a0[TS], a1[TS];
+#pragma unroll
+                        for (int s = 0; s < TS; ++s) { a0[s] = 0.f; a1[s] = 0.f; }
+                        if (valid) {
+                            const float2 *grow = m.g01 + (size_t)r * NW + cc;
+                            for (int col0 = l4; col0 < W; col0 += 16) {
+                                float2 gv[4];
+#pragma unroll
+                                for (int uu = 0; uu < 4; ++uu) {
+                                    const int col = col0 + 4 * uu;
+                                    gv[uu] = col < W ? __ldg(grow + col) : make_float2(0.f, 0.f);
+                                }
+#pragma unroll
+                                for (int uu = 0; uu < 4; ++uu) {
+                                    const int col = min(col0 + 4 * uu, W - 1);
+#pragma unroll
+                                    for (int s = 0; s < TS; ++s) {
+                                        const float e = E[col * TS + s];
+                                        a0[s] = fmaf(gv[uu].x, e, a0[s]);
+                                        a1[s] = fmaf(gv[uu].y, e, a1[s]);
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int s = 0; s < TS; ++s) {
+                            a0[s] += __shfl_xor_sync(0xffffffffu, a0[s], 1);
+                            a1[s] += __shfl_xor_sync(0xffffffffu, a1[s], 1);
+                            a0[s] += __shfl_xor_sync(0xffffffffu, a0[s], 2);
+                            a1[s] += __shfl_xor_sync(0xffffffffu, a1[s], 2);
+                        }
+                        if (valid && l4 == 0) {
+#pragma unroll
+                            for (int s = 0; s < TS; ++s) {
+                                D[(r * TS + s) * 2] += a0[s];
+                                D[(r * TS + s) * 2 + 1] += a1[s];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+
+                // 4. epilogue per (observation, sample): bandflux, residual, chi^2, gradient terms, adjoint rows
+                double chi_acc[TS];
+                float g[TS][6];
+#pragma unroll
+                for (int s = 0; s < TS; ++s) {
+                    chi_acc[s] = 0.0;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) g[s][q] = 0.f;
+                }
+                for (int base = 0; base < nb_obs; base += 32) {
+                    const int il = base + lane;
+                    const bool act = il < nb_obs;
+                    const int i = act ? ordb[il] : 0;
+                    const int64_t gi = obase + i;
+                    const double mj = act ? b.mjd[gi] : 0.0;
+                    const float zpf = act ? sZpf[i] : 0.f;
+                    const float fl = (act && MODE != MODE_BANDFLUX) ? b.flux[gi] : 0.f;
+                    const float sig = (act && MODE != MODE_BANDFLUX) ? b.fluxerr[gi] : 1.f;
+#pragma unroll
+                    for (int s = 0; s < TS; ++s) {
+                        const int j = j0 + s;
+                        Taps4 tp;
+                        tp.first = -1;
+                        float Bs = 0.f, Bp = 0.f, B1 = 0.f, coef = 0.f;
+                        const bool okj = s < ns && sPj[PJ_OK * NJ_MAX + j] != 0.f;
+                        if (act && s < ns) {
+                            const float a = sPj[PJ_A * NJ_MAX + j], x0 = sPj[PJ_X0 * NJ_MAX + j];
+                            const float x1 = sPj[PJ_X1 * NJ_MAX + j];
+                            const float p = (float)(mj - sT0[j]) * a;
+                            int iv; float t;
+                            if (okj && axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
+                                axis_taps_from<GRAD>(iv, t, NP, m.inv_dphase, tp);
+#pragma unroll
+                                for (int mm = 0; mm < 4; ++mm) {
+                                    const float2 dv = *reinterpret_cast<const float2 *>(D + ((tp.first + mm) * TS + s) * 2);
+                                    const float h = fmaf(x1, dv.y, dv.x);
+                                    Bs = fmaf(tp.w[mm], h, Bs);
+                                    if (GRAD) {
+                                        Bp = fmaf(tp.dw[mm], h, Bp);
+                                        B1 = fmaf(tp.w[mm], dv.y, B1);
+                                    }
+                                }
+                            } else {
+                                tp.first = -1;
+                            }
+                            const float pre = x0 * a * zpf;
+                            const float B = pre * Bs;
+                            if (MODE == MODE_BANDFLUX) {
+                                o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + j) * nobs + (oc + i)] = B;
+                            } else {
+                                const float r = (fl - B) / sig;
+                                chi_acc[s] = fma((double)r, (double)r, chi_acc[s]);
+                                if (GRAD) {
+                                    const float gg = -2.0f * r / sig;
+                                    g[s][0] += gg * (-a * B - pre * a * p * Bp);
+                                    g[s][1] += gg * pre * Bp * (-a);
+                                    g[s][2] += gg * a * zpf * Bs;
+                                    g[s][3] += gg * pre * B1;
+                                    coef = gg * pre;
+                                }
+                            }
+                        }
+                        if (GRAD) {
+#pragma unroll
+                            for (int mm = 0; mm < 4; ++mm) {
+                                const bool has = tp.first >= 0;
+                                const int key = has ? tp.first + mm : -1 - lane;
+                                yval[lane] = has ? coef * tp.w[mm] : 0.f;
+                                __syncwarp();
+                                const unsigned grp = __match_any_sync(0xffffffffu, key);
+                                if (has && lane == __ffs(grp) - 1) {
+                                    float sum = 0.f;
+                                    unsigned g2 = grp;
+                                    while (g2) {
+                                        sum += yval[__ffs(g2) - 1];
+                                        g2 &= g2 - 1;
+                                    }
+                                    Y[key * TS + s] += sum;
+                                }
+                                __syncwarp();
+                            }
+                        }
+                    }
+                }
+                (void)ykey;
+
+                // 5. reverse: Q_s[col] = sum_r Y[r][s] H_s[r][col], dotted with E_c, E_z
+                if (GRAD) {
+                    for (int ch = 0; ch < nch; ++ch) {
+                        const int cc = clo + ch * WMAXW;
+                        const int W = min(WMAXW, chi - cc + 1);
+                        if (!one) {
+                            for (int q = lane; q < 2 * WMAXW * TS; q += 32) E[WMAXW * TS + q] = 0.f;
+                            __syncwarp();
+#pragma unroll
+                            for (int s = 0; s < TS; ++s) {
+                                if (s >= ns || kf[s] > kl[s]) continue;
+                                const float a = sPj[PJ_A * NJ_MAX + j0 + s], c = sPj[PJ_C * NJ_MAX + j0 + s];
+                                fk::ebuild<3, false>(m, lam, wk, kf[s], kl[s], kf[s], 32, a, c, cc, W, lane, kc, F,
+                                                     kw, E + s, E + WMAXW * TS + s, E + 2 * WMAXW * TS + s, TS);
+                            }
+                        }
+                        __syncwarp();
+                        for (int col = lane; col < W; col += 32) {
+                            float q0[TS], q1[TS];
+#pragma unroll
+                            for (int s = 0; s < TS; ++s) { q0[s] = 0.f; q1[s] = 0.f; }
+                            const float2 *gcol = m.g01 + cc + col;
+                            for (int rr0 = 0; rr0 < nrows; rr0 += 4) {
+                                float2 gv[4];
+                                int rv[4];
+#pragma unroll
+                                for (int uu = 0; uu < 4; ++uu) {
+                                    rv[uu] = rr0 + uu < nrows ? rowl[rr0 + uu] : -1;
+                                    gv[uu] = rv[uu] >= 0 ? __ldg(gcol + (size_t)rv[uu] * NW) : make_float2(0.f, 0.f);
+                                }
+#pragma unroll
+                                for (int uu = 0; uu < 4; ++uu) {
+                                    if (rv[uu] < 0) continue;
+#pragma unroll
+                                    for (int s = 0; s < TS; ++s) {
+                                        const float y = Y[rv[uu] * TS + s];
+                                        q0[s] = fmaf(y, gv[uu].x, q0[s]);
+                                        q1[s] = fmaf(y, gv[uu].y, q1[s]);
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int s = 0; s < TS; ++s) {
+                                if (s >= ns) continue;
+                                const float qv = fmaf(sPj[PJ_X1 * NJ_MAX + j0 + s], q1[s], q0[s]);
+                                g[s][4] = fmaf(qv, E[WMAXW * TS + col * TS + s], g[s][4]);
+                                g[s][5] = fmaf(qv, E[2 * WMAXW * TS + col * TS + s], g[s][5]);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+
+                // 6. unit partials -> slot[sample][band index]
+                if (MODE != MODE_BANDFLUX) {
+#pragma unroll
+                    for (int s = 0; s < TS; ++s) {
+                        const double x2 = warp_sum_d(chi_acc[s]);
+                        float gs[6];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) gs[q] = GRAD ? warp_sum(g[s][q]) : 0.f;
+                        if (lane == 0 && s < ns) {
+                            double *sl = sSlot + ((size_t)(j0 + s) * NB + bd) * NSLOT;
+                            sl[0] += x2;
+#pragma unroll
+                            for (int q = 0; q < 6; ++q) sl[1 + q] += gs[q];
+                        }
+                    }
+                }
+                __syncwarp();
+            }  // units
+        }  // observation chunks
+
+        __syncthreads();
+        if (MODE != MODE_BANDFLUX) {
+            if (tid < nj) {
+                const int j = tid;
+                double x2 = 0.0;
+                float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int bd = 0; bd < NB; ++bd) {  // band order, absent bands hold zeros
+                    const double *sl = sSlot + ((size_t)j * NB + bd) * NSLOT;
+                    x2 += sl[0];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) g[q] += (float)sl[1 + q];
+                }
+                const bool bad = sPj[PJ_OK * NJ_MAX + j] == 0.f || sMisc[2] != 0;
+                const int64_t gj = wi.par0 + j;
+                o.chi2[gj] = bad ? __longlong_as_double(0x7ff8000000000000ll) : x2;
+                if (GRAD) {
+                    const float gout[5] = {g[0] + g[5], g[1], g[2], g[3], g[4]};
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) o.grad[5 * gj + q] = bad ? fk::qnanf() : gout[q];
+                }
+            }
+        } else {
+            for (int j = 0; j < nj; ++j) {
+                const bool bad = sPj[PJ_OK * NJ_MAX + j] == 0.f || sMisc[2] != 0;
+                if (bad)
+                    for (int64_t i = tid; i < nobs; i += THREADS)
+                        o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + j) * nobs + i] = fk::qnanf();
+            }
+        }
+    }
+}
+
+}  // namespace bw
+
+int bandwarp_item_samples() { return bw::NJ_MAX; }
+int bandwarp_max_phase() { return bw::NPHW; }
+
+template <int TS, int MODE>
+static cudaError_t launch_bw(const salt_ctx *ctx, const WorkItem *items_d, int n_items, int *counter_d,
+                             const BatchDev &b, const OutDev &o, cudaStream_t st) {
+    const int nb = ctx->mp.bands.n_bands;
+    const size_t smem = bw::Lay(TS, MODE == MODE_GRAD, nb).total;
+    static std::atomic<int> attr_done[64];
+    cudaError_t e;
+    const int dv = ctx->device & 63;
+    if (!attr_done[dv].load()) {
+        e = cudaFuncSetAttribute(bw::k_bandwarp<TS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bw::Lay(TS, MODE == MODE_GRAD, SALT_MAX_BANDS).total);
+        if (e != cudaSuccess) return e;
+        attr_done[dv].store(1);
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bw::k_bandwarp<TS, MODE>, bw::THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = ctx->num_sms * per_sm;
+    if (grid > n_items) grid = n_items;
+    if (grid < 1) return cudaSuccess;
+    e = cudaMemsetAsync(counter_d, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    bw::k_bandwarp<TS, MODE><<<grid, bw::THREADS, smem, st>>>(ctx->mp, b, o, items_d, n_items, counter_d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bandwarp_items(const salt_ctx *ctx, int ts, const WorkItem *items_d, int n_items,
+                                  int *counter_d, const BatchDev &b, const OutDev &o, int mode,
+                                  cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    if (ts == 2) {
+        switch (mode) {
+            case MODE_BANDFLUX: return launch_bw<2, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, b, o, st);
+            case MODE_CHI2: return launch_bw<2, MODE_CHI2>(ctx, items_d, n_items, counter_d, b, o, st);
+            default: return launch_bw<2, MODE_GRAD>(ctx, items_d, n_items, counter_d, b, o, st);
+        }
+    }
+    switch (mode) {
+        case MODE_BANDFLUX: return launch_bw<1, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, b, o, st);
+        case MODE_CHI2: return launch_bw<1, MODE_CHI2>(ctx, items_d, n_items, counter_d, b, o, st);
+        default: return launch_bw<1, MODE_GRAD>(ctx, items_d, n_items, counter_d, b, o, st);
+    }
+}
+
+}  // namespace salt

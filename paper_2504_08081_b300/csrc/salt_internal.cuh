@@ -81,10 +81,11 @@ struct WorkItem {
     int32_t nobs, nj, jloc0, pad;
 };
 
-struct Tuning {
-    int tile_samples = 8;    // samples per tile inside an item
-    int tiles_per_item = 1;  // tiles an item walks through (G-window reuse in L1)
-};
+// Launch configurations of the factorised path: kernel family and tile.
+enum Family : int { FAM_CTA = 0, FAM_WARP = 1 };
+inline int cfg_key(int family, int tile) { return family * 16 + tile; }
+inline int cfg_family(int key) { return key / 16; }
+inline int cfg_tile(int key) { return key % 16; }
 
 }  // namespace salt
 
@@ -94,10 +95,14 @@ struct salt_plan {
     int64_t n_sn = 0, n_obs = 0, n_par = 0, n_bandflux = 0;
     std::vector<int64_t> obs_off_h, par_off_h, bf_off_h;
     int64_t *obs_off_d = nullptr, *par_off_d = nullptr, *bf_off_d = nullptr;
-    salt::WorkItem *items_d = nullptr;
-    int n_items = 0;
-    int tile = 0, tiles_per_item = 0;
-    int *counter_d = nullptr;  // dynamic work counter of the persistent kernel
+    // work lists, one per launch configuration (family, tile), built on demand
+    struct ItemList {
+        salt::WorkItem *d = nullptr;
+        int n = 0;
+    };
+    std::map<int, ItemList> lists;
+    int choice[3] = {-1, -1, -1};  // tuned configuration key per mode (-1 = not tuned yet)
+    int *counter_d = nullptr;      // dynamic work counter of the persistent kernels
     bool temporary = false;
     // captured CUDA graphs keyed by the launch signature
     struct GraphEntry {
@@ -133,11 +138,15 @@ namespace salt {
 // Launchers (kernels.cu).
 cudaError_t launch_direct(const salt_ctx *ctx, const BatchDev &b, const OutDev &o, int mode,
                           cudaStream_t st);
-cudaError_t launch_factorised(const salt_ctx *ctx, const salt_plan *plan, const BatchDev &b,
-                              const OutDev &o, int mode, cudaStream_t st);
+
 cudaError_t launch_factorised_items(const salt_ctx *ctx, int tile, const WorkItem *items_d, int n_items,
                                     int *counter_d, const BatchDev &b, const OutDev &o, int mode,
                                     cudaStream_t st);
+cudaError_t launch_bandwarp_items(const salt_ctx *ctx, int ts, const WorkItem *items_d, int n_items,
+                                  int *counter_d, const BatchDev &b, const OutDev &o, int mode,
+                                  cudaStream_t st);
+int bandwarp_item_samples();
+int bandwarp_max_phase();
 cudaError_t launch_validate(const salt_ctx *ctx, const BatchDev &b, int *flag, cudaStream_t st);
 int factorised_smem_bytes(int tile, int mode);
 int factorised_max_tile();
