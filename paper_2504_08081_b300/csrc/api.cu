@@ -151,16 +151,25 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
         }
         off += K;
     }
-    std::vector<float2> g(ng);
-    for (size_t q = 0; q < ng; ++q) g[q] = make_float2(md->m0[q], md->m1[q]);
+    mp.bands.k_total = off;
+    // interleaved (M0, M1) rows with an even pitch so every row starts on 16 bytes
+    const int nwp = md->n_wave + (md->n_wave & 1);
+    mp.nw_pitch = nwp;
+    const size_t ngp = (size_t)md->n_phase * nwp;
+    std::vector<float2> g(ngp, make_float2(0.f, 0.f));
+    for (int r = 0; r < md->n_phase; ++r)
+        for (int j = 0; j < md->n_wave; ++j) {
+            const size_t q = (size_t)r * md->n_wave + j;
+            g[(size_t)r * nwp + j] = make_float2(md->m0[q], md->m1[q]);
+        }
 
     auto fail = [&](cudaError_t err, const char *what) {
         int code = cuda_err(nullptr, err, what);
         salt_destroy(ctx);
         return code;
     };
-    if ((e = cudaMalloc(&ctx->g01_d, ng * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc grid");
-    if ((e = cudaMemcpy(ctx->g01_d, g.data(), ng * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMalloc(&ctx->g01_d, ngp * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc grid");
+    if ((e = cudaMemcpy(ctx->g01_d, g.data(), ngp * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "upload grid");
     const size_t nk = std::max<size_t>(lam_h.size(), 1);
     if ((e = cudaMalloc(&ctx->band_lam_d, nk * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc bands");
@@ -587,6 +596,8 @@ extern "C" int salt_check(salt_ctx *ctx, void *cuda_stream) {
     CK(cudaStreamSynchronize(st), "synchronize");
     CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), st), "clear error word");
     CK(cudaStreamSynchronize(st), "synchronize");
+    if (flag & ERRBIT_TIMEOUT)
+        return set_err(ctx, SALT_ERR_TIMEOUT, "a kernel gave up waiting for a shared-memory copy");
     if (flag)
         return set_err(ctx, SALT_ERR_DATA, (flag & ERRBIT_BAND) ? "a kernel met a band id out of range"
                                            : (flag & ERRBIT_SIGMA) ? "a kernel met fluxerr <= 0"

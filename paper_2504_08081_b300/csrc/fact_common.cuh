@@ -17,90 +17,92 @@ __device__ __forceinline__ int first_tap(int iv, int n) {
 }
 
 // Column-response build for one sample over band samples [kf, kl], columns
-// [cc, cc + W) of the current chunk, by one warp (k-chunks of 32 strided by
-// `stride`). Per k: rest wavelength, Keys taps, colour law, colour factor and
-// trapezoid weight (staged per lane); then per column the contributions of
-// the k whose 4 taps cover it, in increasing k. NEB selects E only (1) or
-// E, E_c, E_z (3); WANT0 = false skips E (rebuild of E_c, E_z only).
-template <int NEB, bool WANT0>
-__device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, const float *wk, int kf,
-                                       int kl, int k_begin, int stride, float a, float c, int cc, int W,
-                                       int lane, int *kc, int *F, float *kw, float *e0, float *e1,
-                                       float *e2, int estride) {
-    constexpr bool GRAD = NEB == 3;
+// [cc, cc + W) of the current chunk, by one warp (chunks of 32 band samples
+// strided by `stride`). Per band sample k (one per lane): rest wavelength,
+// Keys taps, colour law, colour factor and trapezoid weight. Band sample k
+// contributes to columns first_k .. first_k + 3 and first_k is nondecreasing
+// in k, so for each tap the lanes sharing a column form contiguous runs: a
+// segmented inclusive scan (shuffles, fixed tree, as many steps as the
+// longest run needs) sums each run and its last lane adds the total to the
+// column. e0 points at column cc, columns `estride` apart.
+__device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, const float *wk, int kl, int k_begin,
+                                       int stride, float a, float c, int cc, int W, int lane, float *e0,
+                                       int estride) {
     const int NW = m.n_wave;
     for (int k0 = k_begin; k0 <= kl; k0 += stride) {
-        const int nk = min(32, kl - k0 + 1);
-        if (lane < nk) {
-            const int k = k0 + lane;
+        const int k = k0 + lane;
+        const bool act = k <= kl;
+        int first = 0x40000000 + lane;  // inactive lanes: a run of their own, never written
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (act) {
             const float lr = lam[k] * a;
             int iv;
             float t;
             axis_locate(lr, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
             Taps4 tl;
-            axis_taps_from<GRAD>(iv, t, NW, m.inv_dwave, tl);
+            axis_taps_from<false>(iv, t, NW, m.inv_dwave, tl);
             float dcl;
             const float cl = colour_law(m, lr, dcl);
-            const float C = exp2f(kColour * c * cl);
-            const float A = wk[k] * C;
-            kc[lane] = tl.first;
-            float *kwl = kw + lane * 4 * NEB;
+            const float A = wk[k] * exp2f(kColour * c * cl);
+            first = tl.first;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) kwl[q] = A * tl.w[q];
-            if (GRAD) {
-                const float Ac = A * (kColourLn * cl);
-                const float Zs = -A * lr * a;  // d lambda'/dz = -lambda' a
-                const float Zv = Zs * (kColourLn * c * dcl);
+            for (int q = 0; q < 4; ++q) v[q] = A * tl.w[q];
+        }
+        const int fprev = __shfl_up_sync(0xffffffffu, first, 1);
+        const int fnext = __shfl_down_sync(0xffffffffu, first, 1);
+        const bool head = lane == 0 || fprev != first;
+        const bool tail = lane == 31 || fnext != first;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of my run
+        const int runlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    kwl[4 + q] = Ac * tl.w[q];
-                    kwl[8 + q] = fmaf(Zs, tl.dw[q], Zv * tl.w[q]);
-                }
+        for (int q = 0; q < 4; ++q) {
+            float sv = v[q];
+            for (int d = 1; d < runlen; d <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, sv, d);
+                if (lane - d >= start) sv += y;
             }
+            const int col = first + q;
+            if (act && tail && col >= cc && col < cc + W) e0[(col - cc) * estride] += sv;
+            __syncwarp();
         }
-        __syncwarp();
-        const int c0 = kc[0], cl_ = kc[nk - 1];
-        const int span = cl_ - c0;
-        const bool table = span < FSPAN - 1;
-        if (table) {
-            // F[c - c0] = first lane whose first column is >= c, for c in [c0, cl_ + 1]
-            if (lane < nk) {
-                const int prev = lane == 0 ? c0 - 1 : kc[lane - 1];
-                for (int cq = prev + 1; cq <= kc[lane]; ++cq) F[cq - c0] = lane;
-            }
-            if (lane == 0) F[span + 1] = nk;
+    }
+}
+
+// Adjoint of the column response for one sample. With Q[col] = dchi2/dE[col]
+// (the adjoint rows back-projected through the grid) on columns [cc, cc + W),
+// accumulate over band samples [k_begin.., kl] (stride `stride`)
+//   gc += sum_k dA_k/dc        sum_m psi_m(t_k)  Q[first_k + m],
+//   gz += sum_k [ dlambda'_k/dz A_k sum_m dpsi_m/dlambda' Q + dA_k/dz|lambda' sum_m psi_m Q ],
+// i.e. dchi2/dc and the rest-wavelength part of dchi2/dz (A_k = w_k C_k).
+// Lane partials; the caller reduces them.
+__device__ __forceinline__ void eadjoint(const ModelParams &m, const float *lam, const float *wk, int kl, int k_begin,
+                                         int stride, float a, float c, int cc, int W, int lane, const float *Q,
+                                         int qstride, float &gc, float &gz) {
+    const int NW = m.n_wave;
+    for (int k0 = k_begin; k0 <= kl; k0 += stride) {
+        const int k = k0 + lane;
+        if (k > kl) continue;
+        const float lr = lam[k] * a;
+        int iv;
+        float t;
+        axis_locate(lr, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+        Taps4 tl;
+        axis_taps_from<true>(iv, t, NW, m.inv_dwave, tl);
+        float dcl;
+        const float cl = colour_law(m, lr, dcl);
+        const float A = wk[k] * exp2f(kColour * c * cl);
+        float qs = 0.f, qd = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int col = tl.first + q - cc;
+            const float qv = (col >= 0 && col < W) ? Q[col * qstride] : 0.f;
+            qs = fmaf(tl.w[q], qv, qs);
+            qd = fmaf(tl.dw[q], qv, qd);
         }
-        __syncwarp();
-        for (int col = c0 + lane; col <= cl_ + 3; col += 32) {
-            if (col < cc || col >= cc + W) continue;
-            int lo, hi;
-            if (table) {
-                lo = (col - 3 <= c0) ? 0 : F[col - 3 - c0];
-                hi = (col + 1 - c0 > span + 1) ? nk : F[col + 1 - c0];
-            } else {
-                lo = 0; hi = nk;
-                while (lo < hi) { const int md = (lo + hi) >> 1; if (kc[md] >= col - 3) hi = md; else lo = md + 1; }
-                hi = lo;
-                while (hi < nk && kc[hi] <= col) ++hi;
-            }
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int q = lo; q < hi; ++q) {
-                const int mc = col - kc[q];
-                const float *kwq = kw + q * 4 * NEB;
-                if (WANT0) s0 += kwq[mc];
-                if (GRAD) {
-                    s1 += kwq[4 + mc];
-                    s2 += kwq[8 + mc];
-                }
-            }
-            const int ci = (col - cc) * estride;
-            if (WANT0) e0[ci] += s0;
-            if (GRAD) {
-                e1[ci] += s1;
-                e2[ci] += s2;
-            }
-        }
-        __syncwarp();
+        const float Zs = -A * lr * a;  // d lambda'/dz = -lambda' a
+        gc = fmaf(A * (kColourLn * cl), qs, gc);
+        gz = fmaf(Zs, fmaf(kColourLn * c * dcl, qs, qd), gz);
     }
 }
 

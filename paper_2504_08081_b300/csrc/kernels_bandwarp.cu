@@ -14,32 +14,36 @@ namespace bw {
 
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
-constexpr int OBS_MAX = 1024;  // observations of one supernova staged per pass
+constexpr int OBS_MAX = 512;   // observations of one supernova staged per pass
 constexpr int WMAXW = 192;     // window columns per chunk (per warp)
 constexpr int NPHW = 128;      // phase nodes supported by this kernel
 constexpr int NJ_MAX = 16;     // samples per item
 constexpr int NSLOT = 8;       // doubles per (sample, band) partial: chi2, g[6]
+constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memory per CTA
 
 using fk::al16;
 
 struct Lay {
-    size_t ord, zpf, bst, pj, t0, slots, misc, warp0, warp_bytes, total;
+    size_t ord, zpf, band, mjd, flux, sig, bst, pj, t0, slots, misc, lam, wk, warp0, warp_bytes, total;
     __host__ __device__ Lay(int ts, bool grad, int nb) {
-        const int ne = grad ? 3 : 1;
         size_t o = 0;
         ord = o;   o = al16(o + 4 * OBS_MAX);
         zpf = o;   o = al16(o + 4 * OBS_MAX);
+        band = o;  o = al16(o + 4 * OBS_MAX);
+        mjd = o;   o = al16(o + 8 * OBS_MAX);
+        flux = o;  o = al16(o + 4 * OBS_MAX);
+        sig = o;   o = al16(o + 4 * OBS_MAX);
         bst = o;   o = al16(o + 4 * (2 * SALT_MAX_BANDS + 2));
         pj = o;    o = al16(o + 4 * 8 * NJ_MAX);
         t0 = o;    o = al16(o + 8 * NJ_MAX);
         slots = o; o = al16(o + 8 * (size_t)NSLOT * NJ_MAX * (nb > 0 ? nb : 1));
         misc = o;  o = al16(o + 4 * (16 + SALT_MAX_BANDS));
+        lam = o;   o = al16(o + 4 * KTOT);
+        wk = o;    o = al16(o + 4 * KTOT);
         warp0 = o;
-        // per warp: E [ne][WMAXW][ts], D [NPHW][ts][2], Y [NPHW][ts], rows [NPHW],
-        // kc[32], F[FSPAN+2], kw[32][4 ne], ykey[32], yval[32]
-        warp_bytes = al16(4 * (size_t)ne * WMAXW * ts) + al16(4 * (size_t)NPHW * ts * 2) +
-                     al16(grad ? 4 * (size_t)NPHW * ts : 0) + al16(4 * NPHW) +
-                     al16(4 * 32 + 4 * (fk::FSPAN + 2) + 4 * 32 * 4 * ne + 8 * 32);
+        // per warp: E [ne][WMAXW][ts], D [NPHW][ts][2], Y [NPHW][ts], rows [NPHW], yval[32]
+        warp_bytes = al16(4 * (size_t)WMAXW * ts) + al16(4 * (size_t)NPHW * ts * 2) +
+                     al16(grad ? 4 * (size_t)NPHW * ts : 0) + al16(4 * NPHW) + al16(4 * 32);
         o += WARPS * warp_bytes;
         total = o;
     }
@@ -52,12 +56,15 @@ __global__ void __launch_bounds__(THREADS, 2)
 k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items,
            int *counter) {
     constexpr bool GRAD = MODE == MODE_GRAD;
-    constexpr int NE = GRAD ? 3 : 1;
     extern __shared__ __align__(16) unsigned char smem[];
     const int NB = m.bands.n_bands;
     const Lay L(TS, GRAD, NB);
     int *sOrd = (int *)(smem + L.ord);
     float *sZpf = (float *)(smem + L.zpf);
+    int *sBand = (int *)(smem + L.band);
+    double *sMjd = (double *)(smem + L.mjd);
+    float *sFlux = (float *)(smem + L.flux);
+    float *sSig = (float *)(smem + L.sig);
     int *sBst = (int *)(smem + L.bst);
     float *sPj = (float *)(smem + L.pj);  // [5][NJ_MAX]
     double *sT0 = (double *)(smem + L.t0);
@@ -69,23 +76,33 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
     const int NW = m.n_wave, NP = m.n_phase;
 
     unsigned char *wbase = smem + L.warp0 + (size_t)warp * L.warp_bytes;
-    float *E = (float *)wbase;  // [NE][WMAXW][TS]
-    float *D = (float *)(wbase + al16(4 * (size_t)NE * WMAXW * TS));  // [NPHW][TS][2]
+    float *E = (float *)wbase;  // [WMAXW][TS] column responses, then Q
+    float *D = (float *)(wbase + al16(4 * (size_t)WMAXW * TS));  // [NPHW][TS][2]
     float *Y = (float *)((unsigned char *)D + al16(4 * (size_t)NPHW * TS * 2));  // [NPHW][TS]
     int *rowl = (int *)((unsigned char *)Y + al16(GRAD ? 4 * (size_t)NPHW * TS : 0));
-    int *kc = (int *)((unsigned char *)rowl + al16(4 * NPHW));
-    int *F = kc + 32;
-    float *kw = (float *)(F + fk::FSPAN + 2);
-    int *ykey = (int *)(kw + 32 * 4 * NE);
-    float *yval = (float *)(ykey + 32);
+    float *yval = (float *)((unsigned char *)rowl + al16(4 * NPHW));
+    float *sLam = (float *)(smem + L.lam);
+    float *sWk = (float *)(smem + L.wk);
+    const bool bands_staged = m.bands.k_total <= KTOT;
+    if (bands_staged)
+        for (int k = tid; k < m.bands.k_total; k += THREADS) {
+            sLam[k] = __ldg(m.band_lam + k);
+            sWk[k] = __ldg(m.band_w + k);
+        }
 
+    if (tid == 0) sMisc[1] = atomicAdd(counter, 1);
     for (;;) {
         __syncthreads();
-        if (tid == 0) sMisc[0] = atomicAdd(counter, 1);
+        const int it = sMisc[1];
         __syncthreads();
-        const int it = sMisc[0];
         if (it >= n_items) break;
         const WorkItem wi = items[it];
+        if (tid == 0) {
+            // claim the next item now and pull its data into L2 while this one runs
+            const int nxt = atomicAdd(counter, 1);
+            sMisc[1] = nxt;
+            if (nxt < n_items) prefetch_item(b, items[nxt]);
+        }
         const int64_t ob0 = wi.obs0;
         const int64_t nobs = wi.nobs;
         const int nj = wi.nj;  // <= NJ_MAX
@@ -127,6 +144,10 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     sMisc[2] = 1;
                 }
                 sZpf[i] = zp_scale(b.zp[obase + i]);
+                sBand[i] = (okb && e > 0.f) ? bd : -1;
+                sMjd[i] = b.mjd[obase + i];
+                sFlux[i] = b.flux[obase + i];
+                sSig[i] = e;
             }
             __syncthreads();
             if (warp == 0) {
@@ -135,8 +156,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     const int i = base + lane;
                     int bd = -1;
                     if (i < nc) {
-                        bd = b.band[obase + i];
-                        if (bd < 0 || bd >= NB || !(b.fluxerr[obase + i] > 0.f)) bd = -1;
+                        bd = sBand[i];
                     }
                     const unsigned mm = __match_any_sync(0xffffffffu, bd);
                     if (bd >= 0 && lane == __ffs(mm) - 1) cnt[bd] += __popc(mm);
@@ -159,8 +179,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     const int i = base + lane;
                     int bd = -1;
                     if (i < nc) {
-                        bd = b.band[obase + i];
-                        if (bd < 0 || bd >= NB || !(b.fluxerr[obase + i] > 0.f)) bd = -1;
+                        bd = sBand[i];
                     }
                     const unsigned mm = __match_any_sync(0xffffffffu, bd);
                     const int rank = __popc(mm & ((1u << lane) - 1u));
@@ -184,8 +203,8 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                 const int nb_obs = sBst[bd + 1] - sBst[bd];
                 const int *ordb = sOrd + sBst[bd];
                 const int K = m.bands.n[bd], koff = m.bands.off[bd];
-                const float *lam = m.band_lam + koff;
-                const float *wk = m.band_w + koff;
+                const float *lam = (bands_staged ? sLam : m.band_lam) + koff;
+                const float *wk = (bands_staged ? sWk : m.band_w) + koff;
 
                 // 1. in-grid band-sample range per sample (contiguous in k) and union window
                 int kf[TS], kl[TS];
@@ -199,7 +218,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                             const int k = k0 + lane;
                             bool in = false;
                             if (k < K) {
-                                const float lr = __ldg(lam + k) * a;
+                                const float lr = lam[k] * a;
                                 in = lr >= m.wave0 && lr <= m.wave_max;
                             }
                             const unsigned bal = __ballot_sync(0xffffffffu, in);
@@ -210,9 +229,9 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                         }
                         if (kf[s] <= kl[s]) {
                             int iv; float t;
-                            axis_locate(__ldg(lam + kf[s]) * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            axis_locate(lam[kf[s]] * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
                             clo = min(clo, fk::first_tap(iv, NW));
-                            axis_locate(__ldg(lam + kl[s]) * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            axis_locate(lam[kl[s]] * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
                             chi = max(chi, fk::first_tap(iv, NW) + 3);
                         }
                     }
@@ -223,7 +242,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     const int il = base + lane;
                     if (il < nb_obs) {
                         const int i = ordb[il];
-                        const double mj = b.mjd[obase + i];
+                        const double mj = sMjd[i];
 #pragma unroll
                         for (int s = 0; s < TS; ++s) {
                             if (s >= ns || sPj[PJ_OK * NJ_MAX + j0 + s] == 0.f) continue;
@@ -254,25 +273,18 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     for (int q = lane; q < nrows * TS; q += 32) Y[rowl[q / TS] * TS + (q % TS)] = 0.f;
                 __syncwarp();
                 const int nch = (chi >= clo) ? (chi - clo + WMAXW) / WMAXW : 0;
-                const bool one = nch == 1;
 
                 // 3. column response and forward row dots, per column chunk
                 for (int ch = 0; ch < nch; ++ch) {
                     const int cc = clo + ch * WMAXW;
                     const int W = min(WMAXW, chi - cc + 1);
-                    const int nez = (GRAD && one) ? NE : 1;
-                    for (int q = lane; q < nez * WMAXW * TS; q += 32) E[q] = 0.f;
+                    for (int q = lane; q < W * TS; q += 32) E[q] = 0.f;
                     __syncwarp();
 #pragma unroll
                     for (int s = 0; s < TS; ++s) {
                         if (s >= ns || kf[s] > kl[s]) continue;
                         const float a = sPj[PJ_A * NJ_MAX + j0 + s], c = sPj[PJ_C * NJ_MAX + j0 + s];
-                        if (GRAD && one)
-                            fk::ebuild<3, true>(m, lam, wk, kf[s], kl[s], kf[s], 32, a, c, cc, W, lane, kc, F, kw,
-                                                E + s, E + WMAXW * TS + s, E + 2 * WMAXW * TS + s, TS);
-                        else
-                            fk::ebuild<1, true>(m, lam, wk, kf[s], kl[s], kf[s], 32, a, c, cc, W, lane, kc, F, kw,
-                                                E + s, nullptr, nullptr, TS);
+                        fk::ebuild(m, lam, wk, kl[s], kf[s], 32, a, c, cc, W, lane, E + s, TS);
                     }
                     __syncwarp();
                     // 4 lanes per row, 8 rows per pass, 4 columns in flight per lane
@@ -285,16 +297,18 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
 #pragma unroll
                         for (int s = 0; s < TS; ++s) { a0[s] = 0.f; a1[s] = 0.f; }
                         if (valid) {
-                            const float2 *grow = m.g01 + (size_t)r * NW + cc;
-                            for (int col0 = l4; col0 < W; col0 += 16) {
-                                float2 gv[4];
+                            const float2 *grow = m.g01 + (size_t)r * m.nw_pitch + cc;
+                            // UF columns per lane in flight: few dependent L2 round trips per row
+                            constexpr int UF = 16;
+                            for (int col0 = l4; col0 < W; col0 += 4 * UF) {
+                                float2 gv[UF];
 #pragma unroll
-                                for (int uu = 0; uu < 4; ++uu) {
+                                for (int uu = 0; uu < UF; ++uu) {
                                     const int col = col0 + 4 * uu;
                                     gv[uu] = col < W ? __ldg(grow + col) : make_float2(0.f, 0.f);
                                 }
 #pragma unroll
-                                for (int uu = 0; uu < 4; ++uu) {
+                                for (int uu = 0; uu < UF; ++uu) {
                                     const int col = min(col0 + 4 * uu, W - 1);
 #pragma unroll
                                     for (int s = 0; s < TS; ++s) {
@@ -336,11 +350,10 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     const int il = base + lane;
                     const bool act = il < nb_obs;
                     const int i = act ? ordb[il] : 0;
-                    const int64_t gi = obase + i;
-                    const double mj = act ? b.mjd[gi] : 0.0;
+                    const double mj = act ? sMjd[i] : 0.0;
                     const float zpf = act ? sZpf[i] : 0.f;
-                    const float fl = (act && MODE != MODE_BANDFLUX) ? b.flux[gi] : 0.f;
-                    const float sig = (act && MODE != MODE_BANDFLUX) ? b.fluxerr[gi] : 1.f;
+                    const float fl = (act && MODE != MODE_BANDFLUX) ? sFlux[i] : 0.f;
+                    const float sig = (act && MODE != MODE_BANDFLUX) ? sSig[i] : 1.f;
 #pragma unroll
                     for (int s = 0; s < TS; ++s) {
                         const int j = j0 + s;
@@ -407,40 +420,29 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                         }
                     }
                 }
-                (void)ykey;
 
-                // 5. reverse: Q_s[col] = sum_r Y[r][s] H_s[r][col], dotted with E_c, E_z
+                // 5. reverse: Q_s[col] = sum_r Y[r][s] H_s[r][col], then per band sample adjoints
                 if (GRAD) {
                     for (int ch = 0; ch < nch; ++ch) {
                         const int cc = clo + ch * WMAXW;
                         const int W = min(WMAXW, chi - cc + 1);
-                        if (!one) {
-                            for (int q = lane; q < 2 * WMAXW * TS; q += 32) E[WMAXW * TS + q] = 0.f;
-                            __syncwarp();
-#pragma unroll
-                            for (int s = 0; s < TS; ++s) {
-                                if (s >= ns || kf[s] > kl[s]) continue;
-                                const float a = sPj[PJ_A * NJ_MAX + j0 + s], c = sPj[PJ_C * NJ_MAX + j0 + s];
-                                fk::ebuild<3, false>(m, lam, wk, kf[s], kl[s], kf[s], 32, a, c, cc, W, lane, kc, F,
-                                                     kw, E + s, E + WMAXW * TS + s, E + 2 * WMAXW * TS + s, TS);
-                            }
-                        }
                         __syncwarp();
                         for (int col = lane; col < W; col += 32) {
                             float q0[TS], q1[TS];
 #pragma unroll
                             for (int s = 0; s < TS; ++s) { q0[s] = 0.f; q1[s] = 0.f; }
                             const float2 *gcol = m.g01 + cc + col;
-                            for (int rr0 = 0; rr0 < nrows; rr0 += 4) {
-                                float2 gv[4];
-                                int rv[4];
+                            constexpr int UR = 16;  // rows in flight per lane
+                            for (int rr0 = 0; rr0 < nrows; rr0 += UR) {
+                                float2 gv[UR];
+                                int rv[UR];
 #pragma unroll
-                                for (int uu = 0; uu < 4; ++uu) {
+                                for (int uu = 0; uu < UR; ++uu) {
                                     rv[uu] = rr0 + uu < nrows ? rowl[rr0 + uu] : -1;
-                                    gv[uu] = rv[uu] >= 0 ? __ldg(gcol + (size_t)rv[uu] * NW) : make_float2(0.f, 0.f);
+                                    gv[uu] = rv[uu] >= 0 ? __ldg(gcol + (size_t)rv[uu] * m.nw_pitch) : make_float2(0.f, 0.f);
                                 }
 #pragma unroll
-                                for (int uu = 0; uu < 4; ++uu) {
+                                for (int uu = 0; uu < UR; ++uu) {
                                     if (rv[uu] < 0) continue;
 #pragma unroll
                                     for (int s = 0; s < TS; ++s) {
@@ -451,12 +453,16 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                                 }
                             }
 #pragma unroll
-                            for (int s = 0; s < TS; ++s) {
-                                if (s >= ns) continue;
-                                const float qv = fmaf(sPj[PJ_X1 * NJ_MAX + j0 + s], q1[s], q0[s]);
-                                g[s][4] = fmaf(qv, E[WMAXW * TS + col * TS + s], g[s][4]);
-                                g[s][5] = fmaf(qv, E[2 * WMAXW * TS + col * TS + s], g[s][5]);
-                            }
+                            for (int s = 0; s < TS; ++s)
+                                E[col * TS + s] = fmaf(sPj[PJ_X1 * NJ_MAX + j0 + min(s, ns - 1)], q1[s], q0[s]);
+                        }
+                        __syncwarp();
+                        // adjoint of the column response per band sample (E now holds Q)
+#pragma unroll
+                        for (int s = 0; s < TS; ++s) {
+                            if (s >= ns || kf[s] > kl[s]) continue;
+                            const float a = sPj[PJ_A * NJ_MAX + j0 + s], c = sPj[PJ_C * NJ_MAX + j0 + s];
+                            fk::eadjoint(m, lam, wk, kl[s], kf[s], 32, a, c, cc, W, lane, E + s, TS, g[s][4], g[s][5]);
                         }
                         __syncwarp();
                     }

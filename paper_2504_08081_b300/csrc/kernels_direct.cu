@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_direct(ModelParams m, BatchDev b, OutDe
             float M0 = 0.f, M1 = 0.f, M0p = 0.f, M1p = 0.f, M0l = 0.f, M1l = 0.f;
 #pragma unroll
             for (int ra = 0; ra < 4; ++ra) {
-                const float2 *row = m.g01 + (size_t)(tp.first + ra) * m.n_wave + tl.first;
+                const float2 *row = m.g01 + (size_t)(tp.first + ra) * m.nw_pitch + tl.first;
                 float r0 = 0.f, r1 = 0.f, rl0 = 0.f, rl1 = 0.f;
 #pragma unroll
                 for (int cb = 0; cb < 4; ++cb) {

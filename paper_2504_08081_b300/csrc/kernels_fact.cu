@@ -30,35 +30,38 @@ namespace fk {
 
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
-constexpr int OBS_MAX = 1024;  // observations of one supernova staged per pass
+constexpr int OBS_MAX = 512;   // observations of one supernova staged per pass
 constexpr int WMAX = 256;      // union window columns per column chunk
 constexpr int LPR = 4;         // lanes per row in the forward GEMM
 constexpr int NPH_MAX = 256;   // phase nodes supported
-constexpr int KMAX = 512;      // band samples staged in shared memory
+constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memory per CTA
 
 
 struct Lay {
-    size_t ord, zpf, bst, lam, wk, pj, t0, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, total;
+    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, t0, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, total;
     __host__ __device__ Lay(int tj, bool grad, int n_phase) {
-        const int ne = grad ? 3 : 1;
         const int wps = WARPS / tj;
         size_t o = 0;
         ord = o;     o = al16(o + 4 * OBS_MAX);
         zpf = o;     o = al16(o + 4 * OBS_MAX);
+        band = o;    o = al16(o + 4 * OBS_MAX);
+        mjd = o;     o = al16(o + 8 * OBS_MAX);
+        flux = o;    o = al16(o + 4 * OBS_MAX);
+        sig = o;     o = al16(o + 4 * OBS_MAX);
         bst = o;     o = al16(o + 4 * (2 * SALT_MAX_BANDS + 2));
-        lam = o;     o = al16(o + 4 * KMAX);
-        wk = o;      o = al16(o + 4 * KMAX);
+        lam = o;     o = al16(o + 4 * KTOT);
+        wk = o;      o = al16(o + 4 * KTOT);
         pj = o;      o = al16(o + 4 * 8 * tj);
         t0 = o;      o = al16(o + 8 * tj);
         rowmask = o; o = al16(o + 4 * (NPH_MAX / 32));
         rows = o;    o = al16(o + 4 * NPH_MAX);
         misc = o;    o = al16(o + 4 * 16);
-        E = o;       o = al16(o + 4 * (size_t)WMAX * tj * ne);
-        Ep = o;      o = al16(o + (wps > 1 ? 4 * (size_t)WARPS * WMAX * ne : 0));
+        E = o;       o = al16(o + 4 * (size_t)WMAX * tj);
+        Ep = o;      o = al16(o + (wps > 1 ? 4 * (size_t)WARPS * WMAX : 0));
         Q = o;       o = al16(o + (grad ? 4 * (size_t)THREADS * tj : 0));
         D = o;       o = al16(o + 4 * (size_t)n_phase * tj * 2);
         Yw = o;      o = al16(o + (grad ? 4 * (size_t)WARPS * n_phase : 0));
-        kst = o;     o = al16(o + (size_t)WARPS * (4 * 32 + 4 * (FSPAN + 2) + 4 * 32 * 4 * ne + 8 * 32));
+        kst = o;     o = al16(o + (size_t)WARPS * 8 * 32);
         red = o;     o = al16(o + 8 * (size_t)WARPS * 8);
         total = o;
     }
@@ -67,12 +70,78 @@ struct Lay {
 // per-sample scalar slots in Lay::pj
 enum { PJ_A = 0, PJ_X0, PJ_X1, PJ_C, PJ_OK, PJ_KF, PJ_KL, PJ_NUM };
 
+// Row dot of one touched row against the column responses of the tile:
+// acc[j] += sum_col G[row][col] E[col][j] over this lane's columns.
+template <int TJ, bool SMEM>
+__device__ __forceinline__ void fwd_row_dot(const float2 *grow, int W, int l4, const float *sE, float *acc0,
+                                            float *acc1) {
+    constexpr int U = 8;
+    for (int col0 = l4; col0 < W; col0 += U * LPR) {
+        float2 gv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int col = col0 + u * LPR;
+            gv[u] = col < W ? (SMEM ? grow[col] : __ldg(grow + col)) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int col = min(col0 + u * LPR, W - 1);
+            const float *ev = sE + col * TJ;
+            if (TJ % 4 == 0) {
+#pragma unroll
+                for (int j = 0; j < TJ; j += 4) {
+                    const float4 e4 = *reinterpret_cast<const float4 *>(ev + j);
+                    acc0[j] = fmaf(gv[u].x, e4.x, acc0[j]); acc1[j] = fmaf(gv[u].y, e4.x, acc1[j]);
+                    acc0[j + 1] = fmaf(gv[u].x, e4.y, acc0[j + 1]); acc1[j + 1] = fmaf(gv[u].y, e4.y, acc1[j + 1]);
+                    acc0[j + 2] = fmaf(gv[u].x, e4.z, acc0[j + 2]); acc1[j + 2] = fmaf(gv[u].y, e4.z, acc1[j + 2]);
+                    acc0[j + 3] = fmaf(gv[u].x, e4.w, acc0[j + 3]); acc1[j + 3] = fmaf(gv[u].y, e4.w, acc1[j + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < TJ; ++j) {
+                    acc0[j] = fmaf(gv[u].x, ev[j], acc0[j]);
+                    acc1[j] = fmaf(gv[u].y, ev[j], acc1[j]);
+                }
+            }
+        }
+    }
+}
+
+// Back-projection of the adjoint rows onto one column, over the rows
+// rs, rs + nrs, ...: q[j] += sum_r Y[r][j] G[r][col]. With SMEM the grid rows
+// are the staged window's slots (slot = position in the touched-row list).
+template <int TJ, bool SMEM>
+__device__ __forceinline__ void rev_col_dot(const float2 *gcol, size_t stride, const int *sRows, int rs, int nrs,
+                                            int nrows, const float *sY, float *q0, float *q1) {
+    constexpr int U = 8;
+    for (int rr0 = rs; rr0 < nrows; rr0 += U * nrs) {
+        float2 gv[U];
+        int rv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int rr = rr0 + u * nrs;
+            rv[u] = rr < nrows ? sRows[rr] : -1;
+            gv[u] = rv[u] < 0 ? make_float2(0.f, 0.f)
+                              : (SMEM ? gcol[(size_t)rr * stride] : __ldg(gcol + (size_t)rv[u] * stride));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (rv[u] < 0) continue;
+            const float *yv = sY + rv[u] * TJ;
+#pragma unroll
+            for (int j = 0; j < TJ; ++j) {
+                q0[j] = fmaf(yv[j], gv[u].x, q0[j]);
+                q1[j] = fmaf(yv[j], gv[u].y, q1[j]);
+            }
+        }
+    }
+}
+
 template <int TJ, int MODE>
 __global__ void __launch_bounds__(THREADS, 3)
 k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items,
        int *counter) {
     constexpr bool GRAD = MODE == MODE_GRAD;
-    constexpr int NE = GRAD ? 3 : 1;
     constexpr int WPS = WARPS / TJ;  // warps per sample
     extern __shared__ __align__(16) unsigned char smem[];
     const Lay L(TJ, GRAD, m.n_phase);
@@ -86,12 +155,15 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     unsigned *sRowMask = (unsigned *)(smem + L.rowmask);
     int *sRows = (int *)(smem + L.rows);
     int *sMisc = (int *)(smem + L.misc);
-    float *sE = (float *)(smem + L.E);     // [NE][WMAX][TJ]
-    float *sEp = (float *)(smem + L.Ep);   // [NE][WARPS][WMAX] (WPS > 1)
+    float *sE = (float *)(smem + L.E);     // [WMAX][TJ] column responses (then Q)
+    float *sEp = (float *)(smem + L.Ep);   // [WARPS][WMAX] per-warp partials (WPS > 1)
     float *sQ = (float *)(smem + L.Q);     // [THREADS][TJ] reverse-GEMM partials, then Q[col][j]
     float *sD = (float *)(smem + L.D);     // [n_phase][TJ][2]
     float *sYw = (float *)(smem + L.Yw);   // [WARPS][n_phase] adjoint rows per warp
-    unsigned char *kst = smem + L.kst;
+    double *sMjd = (double *)(smem + L.mjd);
+    int *sBand = (int *)(smem + L.band);
+    float *sFlux = (float *)(smem + L.flux);
+    float *sSig = (float *)(smem + L.sig);
     double *sRed = (double *)(smem + L.red);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -99,22 +171,32 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     const int NW = m.n_wave;
     const int NP = m.n_phase;
     // per-warp staging for the column-response build and the adjoint scatter
-    const size_t kst_warp = 4 * 32 + 4 * (FSPAN + 2) + 4 * 32 * 4 * NE + 8 * 32;
-    int *kc = (int *)(kst + warp * kst_warp);
-    int *F = kc + 32;
-    float *kw = (float *)(F + FSPAN + 2);
-    int *ykey = (int *)(kw + 32 * 4 * NE);
-    float *yval = (float *)(ykey + 32);
+    float *yval = (float *)(smem + L.kst) + warp * 64;  // per-warp adjoint scatter staging
+    // every band's samples stay in shared memory for the CTA's lifetime
+    const bool bands_staged = m.bands.k_total <= KTOT;
+    if (bands_staged)
+        for (int k = tid; k < m.bands.k_total; k += THREADS) {
+            sLam[k] = __ldg(m.band_lam + k);
+            sWk[k] = __ldg(m.band_w + k);
+        }
 
+    if (tid == 0) sMisc[1] = atomicAdd(counter, 1);
     for (;;) {
         __syncthreads();
-        if (tid == 0) sMisc[0] = atomicAdd(counter, 1);
+        const int it = sMisc[1];
         __syncthreads();
-        const int it = sMisc[0];
         if (it >= n_items) break;
         const WorkItem wi = items[it];
+        if (tid == 0) {
+            // claim the next item now and pull its data into L2 while this one runs
+            const int nxt = atomicAdd(counter, 1);
+            sMisc[1] = nxt;
+            if (nxt < n_items) prefetch_item(b, items[nxt]);
+        }
         const int64_t ob0 = wi.obs0;
         const int64_t nobs = wi.nobs;
+        if (tid == 0) sMisc[2] = 0;  // any invalid observation in this supernova
+        const bool one_obs_chunk = nobs <= OBS_MAX;
 
         for (int jt = 0; jt < wi.nj; jt += TJ) {
             const int nj = min(TJ, wi.nj - jt);
@@ -143,7 +225,6 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                 sPj[PJ_OK * TJ + j] = (j < nj && ok) ? 1.f : 0.f;
                 sT0[j] = t0;
             }
-            if (tid == 0) sMisc[2] = 0;  // any invalid observation in this supernova
             // per-lane accumulators with a fixed assignment (deterministic sums):
             // warp w owns sample w / WPS in the epilogue and the reverse dot
             double chi_acc = 0.0;
@@ -152,7 +233,9 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             for (int64_t oc = 0; oc < nobs; oc += OBS_MAX) {
                 const int nc = (int)min((int64_t)OBS_MAX, nobs - oc);
                 const int64_t obase = ob0 + oc;
-                // ---- zero-point scales, validation, stable counting sort by band
+                // ---- observations to shared memory, validation, stable counting sort by
+                // band (once per item when they fit in one pass)
+                if (!one_obs_chunk || jt == 0) {
                 __syncthreads();
                 for (int i = tid; i < 2 * SALT_MAX_BANDS + 2; i += THREADS) sBst[i] = 0;
                 __syncthreads();
@@ -165,6 +248,10 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         sMisc[2] = 1;
                     }
                     sZpf[i] = zp_scale(b.zp[obase + i]);
+                    sBand[i] = (okb && e > 0.f) ? bd : -1;
+                    sMjd[i] = b.mjd[obase + i];
+                    sFlux[i] = b.flux[obase + i];
+                    sSig[i] = e;
                 }
                 __syncthreads();
                 if (warp == 0) {
@@ -173,8 +260,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         const int i = base + lane;
                         int bd = -1;
                         if (i < nc) {
-                            bd = b.band[obase + i];
-                            if (bd < 0 || bd >= NB || !(b.fluxerr[obase + i] > 0.f)) bd = -1;
+                            bd = sBand[i];
                         }
                         const unsigned mm = __match_any_sync(0xffffffffu, bd);
                         if (bd >= 0 && lane == __ffs(mm) - 1) cnt[bd] += __popc(mm);
@@ -195,8 +281,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         const int i = base + lane;
                         int bd = -1;
                         if (i < nc) {
-                            bd = b.band[obase + i];
-                            if (bd < 0 || bd >= NB || !(b.fluxerr[obase + i] > 0.f)) bd = -1;
+                            bd = sBand[i];
                         }
                         const unsigned mm = __match_any_sync(0xffffffffu, bd);
                         const int rank = __popc(mm & ((1u << lane) - 1u));
@@ -207,25 +292,20 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     }
                 }
                 __syncthreads();
+                }
 
                 for (int bd = 0; bd < NB; ++bd) {
                     const int nb_obs = sBst[bd + 1] - sBst[bd];
                     if (nb_obs == 0) continue;  // uniform: sBst is shared
                     const int *ordb = sOrd + sBst[bd];
                     const int K = m.bands.n[bd], koff = m.bands.off[bd];
-                    const bool staged = K <= KMAX;
-                    const float *lam = staged ? sLam : m.band_lam + koff;
-                    const float *wk = staged ? sWk : m.band_w + koff;
+                    const float *lam = (bands_staged ? sLam : m.band_lam) + koff;
+                    const float *wk = (bands_staged ? sWk : m.band_w) + koff;
 
                     // ---- 1. band samples to shared memory; window and rows
                     __syncthreads();
                     if (tid == 0) { sMisc[4] = 0x7fffffff; sMisc[5] = -1; sMisc[6] = 0; }
                     for (int q = tid; q < NPH_MAX / 32; q += THREADS) sRowMask[q] = 0u;
-                    if (staged)
-                        for (int k = tid; k < K; k += THREADS) {
-                            sLam[k] = __ldg(m.band_lam + koff + k);
-                            sWk[k] = __ldg(m.band_w + koff + k);
-                        }
                     if (GRAD)
                         for (int q = tid; q < WARPS * NP; q += THREADS) sYw[q] = 0.f;
                     __syncthreads();
@@ -252,18 +332,30 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             atomicMax(&sMisc[5], first_tap(iv, NW) + 3);
                         }
                     }
-                    // touched phase rows (all obs of the band, all samples of the tile)
-                    for (int q = tid; q < nb_obs * nj; q += THREADS) {
-                        const int il = q / nj, j = q - il * nj;
-                        if (sPj[PJ_OK * TJ + j] == 0.f) continue;
-                        const int i = ordb[il];
-                        const float p = (float)(b.mjd[obase + i] - sT0[j]) * sPj[PJ_A * TJ + j];
-                        int iv; float t;
-                        if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
-                            const int first = first_tap(iv, NP);
-                            const unsigned bits = 0xfu << (first & 31);
-                            atomicOr(&sRowMask[first >> 5], bits);
-                            if ((first & 31) > 28) atomicOr(&sRowMask[(first >> 5) + 1], 0xfu >> (32 - (first & 31)));
+                    // touched phase rows (all obs of the band, all samples of the tile): each
+                    // lane's 4-row pattern is OR-reduced over the warp, one shared atomic per word
+                    for (int qb = warp * 32; qb < nb_obs * nj; qb += THREADS) {
+                        const int q = qb + lane;
+                        int first = -1;
+                        if (q < nb_obs * nj) {
+                            const int il = q / nj, j = q - il * nj;
+                            if (sPj[PJ_OK * TJ + j] != 0.f) {
+                                const int i = ordb[il];
+                                const float p = (float)(sMjd[i] - sT0[j]) * sPj[PJ_A * TJ + j];
+                                int iv; float t;
+                                if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t))
+                                    first = first_tap(iv, NP);
+                            }
+                        }
+                        for (int wd = 0; wd < (NP + 31) / 32; ++wd) {
+                            unsigned bits = 0u;
+                            if (first >= 0) {
+                                const int lo = first - wd * 32;  // rows first..first+3 relative to word wd
+                                if (lo >= 0 && lo < 32) bits |= 0xfu << lo;
+                                else if (lo < 0 && lo > -4) bits |= 0xfu >> (-lo);
+                            }
+                            const unsigned word = __reduce_or_sync(0xffffffffu, bits);
+                            if (lane == 0 && word) atomicOr(&sRowMask[wd], word);
                         }
                     }
                     __syncthreads();
@@ -286,17 +378,14 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         sD[sRows[rr] * TJ * 2 + (q - rr * TJ * 2)] = 0.f;
                     }
                     const int n_cchunks = (C_hi >= C_lo) ? (C_hi - C_lo + WMAX) / WMAX : 0;
-                    const bool one_chunk = n_cchunks == 1;
-
                     // ---- 2. column response + forward GEMM, per column chunk
                     for (int ch = 0; ch < n_cchunks; ++ch) {
                         const int cc = C_lo + ch * WMAX;
                         const int W = min(WMAX, C_hi - cc + 1);
-                        const int ne_now = (GRAD && one_chunk) ? NE : 1;
                         __syncthreads();
-                        for (int q = tid; q < ne_now * WMAX * TJ; q += THREADS) sE[q] = 0.f;
+                        for (int q = tid; q < W * TJ; q += THREADS) sE[q] = 0.f;
                         if (WPS > 1)
-                            for (int q = tid; q < ne_now * WARPS * WMAX; q += THREADS) sEp[q] = 0.f;
+                            for (int q = tid; q < WARPS * WMAX; q += THREADS) sEp[q] = 0.f;
                         __syncthreads();
                         {
                             const int j = warp / WPS, sub = warp % WPS;
@@ -305,25 +394,18 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                 const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
                                 float *e0 = (WPS == 1) ? sE + j : sEp + warp * WMAX;
-                                const int es = (WPS == 1) ? TJ : 1;
-                                const int pst = (WPS == 1) ? WMAX * TJ : WARPS * WMAX;
-                                if (GRAD && one_chunk)
-                                    ebuild<3, true>(m, lam, wk, kf, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane,
-                                                    kc, F, kw, e0, e0 + pst, e0 + 2 * pst, es);
-                                else
-                                    ebuild<1, true>(m, lam, wk, kf, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane,
-                                                    kc, F, kw, e0, nullptr, nullptr, es);
+                                ebuild(m, lam, wk, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane, e0,
+                                       (WPS == 1) ? TJ : 1);
                             }
                         }
                         __syncthreads();
                         if (WPS > 1) {
-                            for (int q = tid; q < ne_now * W * TJ; q += THREADS) {
-                                const int e = q / (W * TJ), rem = q - e * W * TJ;
-                                const int col = rem / TJ, j = rem - col * TJ;
+                            for (int q = tid; q < W * TJ; q += THREADS) {
+                                const int col = q / TJ, j = q - col * TJ;
                                 float acc = 0.f;
 #pragma unroll
-                                for (int sb = 0; sb < WPS; ++sb) acc += sEp[e * WARPS * WMAX + (j * WPS + sb) * WMAX + col];
-                                sE[e * WMAX * TJ + col * TJ + j] = acc;
+                                for (int sb = 0; sb < WPS; ++sb) acc += sEp[(j * WPS + sb) * WMAX + col];
+                                sE[col * TJ + j] = acc;
                             }
                             __syncthreads();
                         }
@@ -338,38 +420,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 float acc0[TJ], acc1[TJ];
 #pragma unroll
                                 for (int j = 0; j < TJ; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
-                                if (valid) {
-                                    const float2 *grow = m.g01 + (size_t)r * NW + cc;
-                                    for (int col0 = l4; col0 < W; col0 += 4 * LPR) {
-                                        float2 gv[4];
-#pragma unroll
-                                        for (int u = 0; u < 4; ++u) {
-                                            const int col = col0 + u * LPR;
-                                            gv[u] = col < W ? __ldg(grow + col) : make_float2(0.f, 0.f);
-                                        }
-#pragma unroll
-                                        for (int u = 0; u < 4; ++u) {
-                                            const int col = min(col0 + u * LPR, W - 1);
-                                            const float *ev = sE + col * TJ;
-                                            if (TJ % 4 == 0) {
-#pragma unroll
-                                                for (int j = 0; j < TJ; j += 4) {
-                                                    const float4 e4 = *reinterpret_cast<const float4 *>(ev + j);
-                                                    acc0[j] = fmaf(gv[u].x, e4.x, acc0[j]); acc1[j] = fmaf(gv[u].y, e4.x, acc1[j]);
-                                                    acc0[j + 1] = fmaf(gv[u].x, e4.y, acc0[j + 1]); acc1[j + 1] = fmaf(gv[u].y, e4.y, acc1[j + 1]);
-                                                    acc0[j + 2] = fmaf(gv[u].x, e4.z, acc0[j + 2]); acc1[j + 2] = fmaf(gv[u].y, e4.z, acc1[j + 2]);
-                                                    acc0[j + 3] = fmaf(gv[u].x, e4.w, acc0[j + 3]); acc1[j + 3] = fmaf(gv[u].y, e4.w, acc1[j + 3]);
-                                                }
-                                            } else {
-#pragma unroll
-                                                for (int j = 0; j < TJ; ++j) {
-                                                    acc0[j] = fmaf(gv[u].x, ev[j], acc0[j]);
-                                                    acc1[j] = fmaf(gv[u].y, ev[j], acc1[j]);
-                                                }
-                                            }
-                                        }
-                                    }
-                                }
+                                if (valid)
+                                    fwd_row_dot<TJ, false>(m.g01 + (size_t)r * m.nw_pitch + cc, W, l4, sE, acc0, acc1);
 #pragma unroll
                                 for (int sh = 1; sh < LPR; sh <<= 1) {
 #pragma unroll
@@ -407,8 +459,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 float Bs = 0.f, Bp = 0.f, B1 = 0.f, coef = 0.f;
                                 if (act) {
                                     const int i = ordb[il];
-                                    const int64_t gi = obase + i;
-                                    const float p = (float)(b.mjd[gi] - t0) * a;
+                                    const float p = (float)(sMjd[i] - t0) * a;
                                     int iv; float t;
                                     if (okj && axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
                                         axis_taps_from<GRAD>(iv, t, NP, m.inv_dphase, tp);
@@ -431,8 +482,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     if (MODE == MODE_BANDFLUX) {
                                         o.bandflux[wi.bf0 + (int64_t)(jloc0 + j) * nobs + (oc + i)] = B;
                                     } else {
-                                        const float sig = b.fluxerr[gi];
-                                        const float r = (b.flux[gi] - B) / sig;
+                                        const float sig = sSig[i];
+                                        const float r = (sFlux[i] - B) / sig;
                                         chi_acc = fma((double)r, (double)r, chi_acc);
                                         if (GRAD) {
                                             const float g = -2.0f * r / sig;
@@ -451,7 +502,6 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     for (int mm = 0; mm < 4; ++mm) {
                                         const bool has = tp.first >= 0;
                                         const int key = has ? tp.first + mm : -1 - lane;
-                                        ykey[lane] = key;
                                         yval[lane] = has ? coef * tp.w[mm] : 0.f;
                                         __syncwarp();
                                         const unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -471,7 +521,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             }
                         }
                     }
-                    // ---- 4. reverse GEMM: Q_j[col] = sum_r Y[r][j] H_j[r][col], dotted with E_c, E_z
+                    // ---- 4. reverse: Q_j[col] = sum_r Y[r][j] H_j[r][col], then per band sample adjoints
                     if (GRAD) {
                         __syncthreads();
                         // combine the per-warp adjoint rows into Y[r][j] (in warp order)
@@ -488,36 +538,6 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             const int cc = C_lo + ch * WMAX;
                             const int W = min(WMAX, C_hi - cc + 1);
                             __syncthreads();
-                            if (!one_chunk) {
-                                // rebuild E_c, E_z for this chunk (wide windows only)
-                                for (int q = tid; q < 2 * WMAX * TJ; q += THREADS) sE[WMAX * TJ + q] = 0.f;
-                                if (WPS > 1)
-                                    for (int q = tid; q < 2 * WARPS * WMAX; q += THREADS) sEp[WARPS * WMAX + q] = 0.f;
-                                __syncthreads();
-                                const int j = warp / WPS, sub = warp % WPS;
-                                if (j < nj && sPj[PJ_OK * TJ + j] != 0.f) {
-                                    const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
-                                    const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
-                                    const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
-                                    float *e0 = (WPS == 1) ? sE + j : sEp + warp * WMAX;
-                                    const int es = (WPS == 1) ? TJ : 1;
-                                    const int pst = (WPS == 1) ? WMAX * TJ : WARPS * WMAX;
-                                    ebuild<3, false>(m, lam, wk, kf, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane, kc,
-                                                     F, kw, e0, e0 + pst, e0 + 2 * pst, es);
-                                }
-                                __syncthreads();
-                                if (WPS > 1) {
-                                    for (int q = tid; q < 2 * W * TJ; q += THREADS) {
-                                        const int e = 1 + q / (W * TJ), rem = q % (W * TJ);
-                                        const int col = rem / TJ, jj = rem - col * TJ;
-                                        float acc = 0.f;
-#pragma unroll
-                                        for (int sb = 0; sb < WPS; ++sb) acc += sEp[e * WARPS * WMAX + (jj * WPS + sb) * WMAX + col];
-                                        sE[e * WMAX * TJ + col * TJ + jj] = acc;
-                                    }
-                                }
-                                __syncthreads();
-                            }
                             // partial Q per (row subset, column): threads = column + row split
                             const int Wp = (W + 31) & ~31;
                             const int nrs = THREADS / Wp;
@@ -526,46 +546,32 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 float q0[TJ], q1[TJ];
 #pragma unroll
                                 for (int j = 0; j < TJ; ++j) { q0[j] = 0.f; q1[j] = 0.f; }
-                                if (col < W && rs < nrs) {
-                                    const float2 *gcol = m.g01 + cc + col;
-                                    for (int rr0 = rs; rr0 < nrows; rr0 += 4 * nrs) {
-                                        float2 gv[4];
-                                        int rv[4];
-#pragma unroll
-                                        for (int u = 0; u < 4; ++u) {
-                                            const int rr = rr0 + u * nrs;
-                                            rv[u] = rr < nrows ? sRows[rr] : -1;
-                                            gv[u] = rv[u] >= 0 ? __ldg(gcol + (size_t)rv[u] * NW) : make_float2(0.f, 0.f);
-                                        }
-#pragma unroll
-                                        for (int u = 0; u < 4; ++u) {
-                                            if (rv[u] < 0) continue;
-                                            const float *yv = sY + rv[u] * TJ;
-#pragma unroll
-                                            for (int j = 0; j < TJ; ++j) {
-                                                q0[j] = fmaf(yv[j], gv[u].x, q0[j]);
-                                                q1[j] = fmaf(yv[j], gv[u].y, q1[j]);
-                                            }
-                                        }
-                                    }
-                                }
+                                if (col < W && rs < nrs)
+                                    rev_col_dot<TJ, false>(m.g01 + cc + col, (size_t)m.nw_pitch, sRows, rs, nrs, nrows,
+                                                           sY, q0, q1);
 #pragma unroll
                                 for (int j = 0; j < TJ; ++j) sQ[tid * TJ + j] = fmaf(sPj[PJ_X1 * TJ + j], q1[j], q0[j]);
                             }
                             __syncthreads();
-                            // dot with E_c, E_z: warp w -> sample w / WPS, columns split by sub
+                            // Q[col][j] = sum over row subsets in order (into the E buffer, free now)
+                            float *sQf = sE;
+                            for (int q = tid; q < W * TJ; q += THREADS) {
+                                const int col = q / TJ, j = q - col * TJ;
+                                float qv = 0.f;
+                                for (int rs = 0; rs < nrs; ++rs) qv += sQ[(rs * Wp + col) * TJ + j];
+                                sQf[col * TJ + j] = qv;
+                            }
+                            __syncthreads();
+                            // adjoint of the column response per band sample: dchi2/dc and the
+                            // rest-wavelength part of dchi2/dz (warp -> sample, band samples split by sub)
                             {
                                 const int j = warp / WPS, sub = warp % WPS;
-                                if (j < nj) {
-                                    float dc = 0.f, dz = 0.f;
-                                    for (int col = sub * 32 + lane; col < W; col += 32 * WPS) {
-                                        float qv = 0.f;
-                                        for (int rs = 0; rs < nrs; ++rs) qv += sQ[(rs * Wp + col) * TJ + j];
-                                        dc = fmaf(qv, sE[WMAX * TJ + col * TJ + j], dc);
-                                        dz = fmaf(qv, sE[2 * WMAX * TJ + col * TJ + j], dz);
-                                    }
-                                    gacc[4] += dc;  // lane partials; reduced at the end of the tile
-                                    gacc[5] += dz;
+                                if (j < nj && sPj[PJ_OK * TJ + j] != 0.f) {
+                                    const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
+                                    const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
+                                    const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
+                                    eadjoint(m, lam, wk, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane, sQf + j, TJ,
+                                             gacc[4], gacc[5]);
                                 }
                             }
                         }

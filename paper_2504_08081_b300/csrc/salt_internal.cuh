@@ -20,11 +20,12 @@
 namespace salt {
 
 // Error bits a kernel records in the context's device error word.
-enum : int { ERRBIT_BAND = 1, ERRBIT_SIGMA = 2, ERRBIT_PARAM = 4, ERRBIT_WINDOW = 8 };
+enum : int { ERRBIT_BAND = 1, ERRBIT_SIGMA = 2, ERRBIT_PARAM = 4, ERRBIT_WINDOW = 8, ERRBIT_TIMEOUT = 16 };
 
 // Band table passed by value to every kernel (fits the kernel parameter space).
 struct BandTable {
     int n_bands;
+    int k_total;  // band samples over all bands (flat arrays)
     int off[SALT_MAX_BANDS];  // first sample of band b in the flat arrays
     int n[SALT_MAX_BANDS];    // samples in band b
     float lam_lo[SALT_MAX_BANDS], lam_hi[SALT_MAX_BANDS];  // first / last observer wavelength
@@ -33,13 +34,14 @@ struct BandTable {
 // Model constants in the form the kernels use (FP32, derived on the host in FP64).
 struct ModelParams {
     int n_phase, n_wave;
+    int nw_pitch;  // row pitch of g01 in float2 (n_wave rounded up to even: 16-byte aligned rows)
     float phase0, inv_dphase, phase_max;
     float wave0, inv_dwave, wave_max, dwave;
     // colour law: P(x) = sum_{m=1..5} p[m-1] x^m, x = (lambda - lamB) * inv_span
     float cl_p[5];
     float cl_lamB, cl_inv_span, cl_lo, cl_hi;
     float cl_xlo, cl_Plo, cl_dPlo, cl_xhi, cl_Phi, cl_dPhi;
-    const float2 *__restrict__ g01;      // [n_phase][n_wave] interleaved (M0, M1)
+    const float2 *__restrict__ g01;      // [n_phase][nw_pitch] interleaved (M0, M1)
     const float *__restrict__ band_lam;  // flat band wavelengths (observer frame)
     const float *__restrict__ band_w;    // flat weights lambda T Delta / (h c Z_b)
     BandTable bands;
