@@ -183,7 +183,10 @@ typedef enum {
     SALT_KERNEL_AUTO = 0,        /* factorised path; family and tile autotuned per plan and mode */
     SALT_KERNEL_DIRECT = 1,      /* per-band-sample evaluation straight from Eq. 1-2 */
     SALT_KERNEL_FACTORISED = 2,  /* factorised, CTA-cooperative per (sample tile, band) */
-    SALT_KERNEL_BANDWARP = 3     /* factorised, one warp per (band, 1-2 samples); <= 128 phase nodes */
+    SALT_KERNEL_BANDWARP = 3,    /* factorised, one warp per (band, 1-2 samples); <= 128 phase nodes */
+    SALT_KERNEL_UNIT = 4         /* factorised, warps pull (supernova, band, 1-2 samples) units from a
+                                    global counter; per-band partials combined in band order through
+                                    plan-owned scratch memory; <= 128 phase nodes */
 } salt_kernel;
 
 int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value);

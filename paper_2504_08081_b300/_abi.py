@@ -33,6 +33,7 @@ SALT_KERNEL_AUTO = 0
 SALT_KERNEL_DIRECT = 1
 SALT_KERNEL_FACTORISED = 2
 SALT_KERNEL_BANDWARP = 3
+SALT_KERNEL_UNIT = 4
 
 # Every symbol include/salt.h declares (checked by the ABI test).
 EXPORTS = [

@@ -270,6 +270,8 @@ static int build_items(salt_ctx *ctx, salt_plan *p, int key, cudaStream_t st) {
     int span;
     if (family == FAM_WARP) {
         span = bandwarp_item_samples();
+    } else if (family == FAM_UNIT) {
+        span = tile;
     } else {
         int64_t total_tiles = 0;
         for (int64_t s = 0; s < n_sn; ++s) total_tiles += (po[s + 1] - po[s] + tile - 1) / tile;
@@ -296,6 +298,11 @@ static int build_items(salt_ctx *ctx, salt_plan *p, int key, cudaStream_t st) {
     const size_t bytes = std::max<size_t>(wl.size() * sizeof(WorkItem), 16);
     CK(p->temporary ? cudaMallocAsync((void **)&L.d, bytes, st) : cudaMalloc((void **)&L.d, bytes),
        "alloc work list");
+    if (family == FAM_UNIT) {
+        const size_t sb = unit_scratch_bytes(L.n, tile, ctx->mp.bands.n_bands);
+        CK(p->temporary ? cudaMallocAsync(&L.scratch, sb, st) : cudaMalloc(&L.scratch, sb), "alloc scratch");
+        CK(cudaMemsetAsync(L.scratch, 0, sb, st), "clear scratch");
+    }
     p->lists[key] = L;
     if (!wl.empty()) {
         CK(cudaMemcpyAsync(L.d, wl.data(), wl.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
@@ -311,7 +318,10 @@ void plan_free(salt_plan *p, cudaStream_t st) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     p->graphs.clear();
     std::vector<void *> ptrs = {p->obs_off_d, p->par_off_d, p->bf_off_d, p->counter_d};
-    for (auto &kv : p->lists) ptrs.push_back(kv.second.d);
+    for (auto &kv : p->lists) {
+        ptrs.push_back(kv.second.d);
+        ptrs.push_back(kv.second.scratch);
+    }
     for (void *q : ptrs)
         if (q) {
             if (p->temporary) cudaFreeAsync(q, st); else cudaFree(q);
@@ -326,12 +336,21 @@ static cudaError_t launch_key(salt_ctx *ctx, salt_plan *p, int key, const BatchD
     const salt_plan::ItemList &L = p->lists[key];
     if (cfg_family(key) == FAM_WARP)
         return launch_bandwarp_items(ctx, cfg_tile(key), L.d, L.n, p->counter_d, b, o, mode, st);
+    if (cfg_family(key) == FAM_UNIT)
+        return launch_unit_items(ctx, cfg_tile(key), L.d, L.n, p->counter_d, L.scratch, b, o, mode, st);
     return launch_factorised_items(ctx, cfg_tile(key), L.d, L.n, p->counter_d, b, o, mode, st);
 }
 
 // Heuristic configuration (used for one-off plans and while capturing).
+static bool unit_ok(const salt_ctx *ctx, const salt_plan *p, int ts) {
+    if (ctx->mp.n_phase > unit_max_phase() || ctx->mp.bands.n_bands < 1) return false;
+    const int64_t items = p->n_par / ts + p->n_sn;
+    return unit_scratch_bytes((int)std::min<int64_t>(items, INT32_MAX), ts, ctx->mp.bands.n_bands) <= ((size_t)256 << 20);
+}
+
 static int default_config(const salt_ctx *ctx, const salt_plan *p) {
     const double mean = p->n_sn > 0 ? (double)p->n_par / (double)p->n_sn : 1.0;
+    if (mean < 4 && unit_ok(ctx, p, mean >= 2 ? 2 : 1)) return cfg_key(FAM_UNIT, mean >= 2 ? 2 : 1);
     const bool warp_ok = ctx->mp.n_phase <= bandwarp_max_phase();
     if (warp_ok && mean < 4) return cfg_key(FAM_WARP, mean >= 2 ? 2 : 1);
     if (mean >= 8) return cfg_key(FAM_CTA, 8);
@@ -390,6 +409,8 @@ static int tune(salt_ctx *ctx, salt_plan *p, const BatchDev &b, const OutDev &o,
         cands.push_back(cfg_key(FAM_WARP, 1));
         if (mean >= 1.5) cands.push_back(cfg_key(FAM_WARP, 2));
     }
+    if (unit_ok(ctx, p, 1)) cands.push_back(cfg_key(FAM_UNIT, 1));
+    if (mean >= 1.5 && unit_ok(ctx, p, 2)) cands.push_back(cfg_key(FAM_UNIT, 2));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "tune");
     CK(cudaEventCreate(&e1), "tune");
@@ -430,6 +451,11 @@ int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const Ou
     const int tile = ctx->tile_samples;
     if (ctx->kernel == SALT_KERNEL_FACTORISED) {
         key = cfg_key(FAM_CTA, tile > 0 ? tile : cfg_tile(default_config(ctx, p)));
+    } else if (ctx->kernel == SALT_KERNEL_UNIT) {
+        const int ts = tile == 2 ? 2 : 1;
+        if (!unit_ok(ctx, p, ts))
+            return set_err(ctx, SALT_ERR_INVALID, "warp-unit kernel: >128 phase nodes, no bands or scratch too large");
+        key = cfg_key(FAM_UNIT, ts);
     } else if (ctx->kernel == SALT_KERNEL_BANDWARP) {
         if (ctx->mp.n_phase > bandwarp_max_phase())
             return set_err(ctx, SALT_ERR_INVALID, "band-warp kernel supports at most 128 phase nodes");
@@ -611,7 +637,7 @@ extern "C" int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value) {
     if (!ctx) return SALT_ERR_INVALID;
     switch (option) {
         case SALT_OPT_KERNEL:
-            if (value < 0 || value > 3) return SALT_ERR_INVALID;
+            if (value < 0 || value > 4) return SALT_ERR_INVALID;
             ctx->kernel = (int)value;
             return SALT_OK;
         case SALT_OPT_TILE_SAMPLES:

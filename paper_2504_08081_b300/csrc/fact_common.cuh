@@ -69,6 +69,73 @@ __device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, c
     }
 }
 
+// Forward-mode column responses for one sample: E as ebuild, plus
+//   E_c[col] = sum_k dA_k/dc psi_col(t_k)                          (d E / d c)
+//   E_z[col] = sum_k dlambda'_k/dz (A_k psi'_col + dA_k/dlambda' psi_col)   (d E / d z through lambda')
+// (A_k = w_k C_k), built with the same segmented scan. e0/e1/e2 point at
+// column cc of E, E_c, E_z, columns `estride` apart.
+__device__ __forceinline__ void ebuild3(const ModelParams &m, const float *lam, const float *wk, int kl, int k_begin,
+                                        int stride, float a, float c, int cc, int W, int lane, float *e0, float *e1,
+                                        float *e2, int estride) {
+    const int NW = m.n_wave;
+    for (int k0 = k_begin; k0 <= kl; k0 += stride) {
+        const int k = k0 + lane;
+        const bool act = k <= kl;
+        int first = 0x40000000 + lane;
+        float v[3][4];
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[e][q] = 0.f;
+        if (act) {
+            const float lr = lam[k] * a;
+            int iv;
+            float t;
+            axis_locate(lr, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+            Taps4 tl;
+            axis_taps_from<true>(iv, t, NW, m.inv_dwave, tl);
+            float dcl;
+            const float cl = colour_law(m, lr, dcl);
+            const float A = wk[k] * exp2f(kColour * c * cl);
+            const float Ac = A * (kColourLn * cl);
+            const float Zs = -A * lr * a;
+            const float Zv = Zs * (kColourLn * c * dcl);
+            first = tl.first;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[0][q] = A * tl.w[q];
+                v[1][q] = Ac * tl.w[q];
+                v[2][q] = fmaf(Zs, tl.dw[q], Zv * tl.w[q]);
+            }
+        }
+        const int fprev = __shfl_up_sync(0xffffffffu, first, 1);
+        const int fnext = __shfl_down_sync(0xffffffffu, first, 1);
+        const bool head = lane == 0 || fprev != first;
+        const bool tail = lane == 31 || fnext != first;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const int runlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float s0 = v[0][q], s1 = v[1][q], s2 = v[2][q];
+            for (int d = 1; d < runlen; d <<= 1) {
+                const float y0 = __shfl_up_sync(0xffffffffu, s0, d);
+                const float y1 = __shfl_up_sync(0xffffffffu, s1, d);
+                const float y2 = __shfl_up_sync(0xffffffffu, s2, d);
+                if (lane - d >= start) { s0 += y0; s1 += y1; s2 += y2; }
+            }
+            const int col = first + q;
+            if (act && tail && col >= cc && col < cc + W) {
+                const int ci = (col - cc) * estride;
+                e0[ci] += s0;
+                e1[ci] += s1;
+                e2[ci] += s2;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Adjoint of the column response for one sample. With Q[col] = dchi2/dE[col]
 // (the adjoint rows back-projected through the grid) on columns [cc, cc + W),
 // accumulate over band samples [k_begin.., kl] (stride `stride`)

@@ -1,0 +1,465 @@
+// Warp-scheduled factorised kernel: every warp independently pulls
+// (supernova, band, group of TS samples) units from a global counter and runs
+// the whole factorised pipeline for its unit (column response, row dots over
+// the touched phase rows, per-observation epilogue) without any block-level
+// barrier. The gradient is forward mode: the column responses E_c = dE/dc and
+// E_z = dE/dz (through lambda') are built beside E, their row dots come from
+// the same grid loads, and the epilogue finishes every derivative, so a unit
+// makes a single pass over its grid window. A unit leaves its (sample, band) partials
+// (chi^2 and gradient terms) in a scratch buffer; the warp that completes a
+// supernova's last band (arrival counter per item) sums the partials in band
+// order and writes the outputs, so results are bitwise reproducible whatever
+// the arrival order. Suited to batches with few samples per supernova, where
+// whole-supernova items leave warps idle behind block barriers.
+#include "fact_common.cuh"
+
+namespace salt {
+namespace uk {
+
+constexpr int THREADS = 256;
+constexpr int WARPS = THREADS / 32;
+constexpr int OBS_W = 128;  // observations of the unit's band cached per pass
+constexpr int WMAXW = 192;  // window columns per chunk
+constexpr int NPHW = 128;   // phase nodes supported by this kernel
+constexpr int KTOT = 2048;  // band samples (all bands) staged in shared memory per CTA
+constexpr int NSLOT = 8;    // doubles per (sample, band) partial: chi2, g[6], invalid flag
+
+using fk::al16;
+
+struct Lay {
+    size_t lam, wk, warp0, warp_bytes, total;
+    __host__ __device__ Lay(int ts, bool grad) {
+        const int ne = grad ? 3 : 1;
+        size_t o = 0;
+        lam = o; o = al16(o + 4 * KTOT);
+        wk = o;  o = al16(o + 4 * KTOT);
+        warp0 = o;
+        // per warp: obs cache (index, mjd, flux, sig, zpf), E (and E_c, E_z) [WMAXW][ts],
+        // row dots D [NPHW][ts][2 ne], row list [NPHW]
+        warp_bytes = al16(4 * OBS_W) + al16(8 * OBS_W) + 3 * al16(4 * OBS_W) + al16(4 * (size_t)WMAXW * ts * ne) +
+                     al16(4 * (size_t)NPHW * ts * 2 * ne) + al16(4 * NPHW);
+        o += WARPS * warp_bytes;
+        total = o;
+    }
+};
+
+struct UnitScratch {
+    double *partial;  // [n_items][ts][n_bands][NSLOT]
+    int *arrive;      // [n_items] bands finished (reset by the combining warp)
+};
+
+template <int TS, int MODE>
+__global__ void __launch_bounds__(THREADS, 3)
+k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items, int *counter,
+       UnitScratch scr) {
+    constexpr bool GRAD = MODE == MODE_GRAD;
+    constexpr int NE = GRAD ? 3 : 1;  // column responses per sample: E (, E_c, E_z)
+    constexpr int ND = 2 * NE;        // row dots per (row, sample): x surfaces M0, M1
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lay L(TS, GRAD);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NB = m.bands.n_bands, NW = m.n_wave, NP = m.n_phase;
+    float *sLam = (float *)(smem + L.lam);
+    float *sWk = (float *)(smem + L.wk);
+    const bool bands_staged = m.bands.k_total <= KTOT;
+    if (bands_staged)
+        for (int k = tid; k < m.bands.k_total; k += THREADS) {
+            sLam[k] = __ldg(m.band_lam + k);
+            sWk[k] = __ldg(m.band_w + k);
+        }
+    __syncthreads();  // the only block barrier: band samples staged
+
+    unsigned char *wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
+    int *oIdx = (int *)wb;                                     wb += al16(4 * OBS_W);
+    double *oMjd = (double *)wb;                               wb += al16(8 * OBS_W);
+    float *oFlux = (float *)wb;                                wb += al16(4 * OBS_W);
+    float *oSig = (float *)wb;                                 wb += al16(4 * OBS_W);
+    float *oZpf = (float *)wb;                                 wb += al16(4 * OBS_W);
+    float *E = (float *)wb;                                    wb += al16(4 * (size_t)WMAXW * TS * NE);
+    float *D = (float *)wb;                                    wb += al16(4 * (size_t)NPHW * TS * ND);
+    int *rowl = (int *)wb;
+
+    const int n_units = n_items * NB;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(counter, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= n_units) break;
+        const int item = u / NB, bd = u - item * NB;
+        const WorkItem wi = items[item];
+        const int64_t ob0 = wi.obs0;
+        const int nobs = wi.nobs;
+        const int ns = wi.nj;  // <= TS
+
+        // per-sample parameters (uniform across the warp)
+        float pa[TS], px0[TS], px1[TS], pc[TS];
+        double pt0[TS];
+        bool pok[TS];
+#pragma unroll
+        for (int s = 0; s < TS; ++s) {
+            pa[s] = 1.f; px0[s] = 0.f; px1[s] = 0.f; pc[s] = 0.f; pt0[s] = 0.0; pok[s] = false;
+            if (s < ns) {
+                const int64_t g = wi.par0 + s;
+                const float z = b.z[g], x0 = b.x0[g], x1 = b.x1[g], c = b.c[g];
+                const double t0 = b.t0[g];
+                pok[s] = isfinite(z) && z > -1.f && isfinite(x0) && isfinite(x1) && isfinite(c) && isfinite(t0);
+                if (pok[s]) { pa[s] = 1.0f / (1.0f + z); px0[s] = x0; px1[s] = x1; pc[s] = c; pt0[s] = t0; }
+                else if (lane == 0 && bd == 0) atomicOr(o.err, ERRBIT_PARAM);
+            }
+        }
+        const int K = m.bands.n[bd], koff = m.bands.off[bd];
+        const float *lam = (bands_staged ? sLam : m.band_lam) + koff;
+        const float *wk = (bands_staged ? sWk : m.band_w) + koff;
+
+        // in-grid band-sample range per sample (contiguous in k) and the union window
+        int kf[TS], kl[TS];
+        int clo = 0x7fffffff, chi = -1;
+#pragma unroll
+        for (int s = 0; s < TS; ++s) {
+            kf[s] = K; kl[s] = -1;
+            if (pok[s]) {
+                for (int k0 = 0; k0 < K; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool in = false;
+                    if (k < K) {
+                        const float lr = lam[k] * pa[s];
+                        in = lr >= m.wave0 && lr <= m.wave_max;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    if (bal) {
+                        if (kf[s] == K) kf[s] = k0 + __ffs(bal) - 1;
+                        kl[s] = k0 + 31 - __clz(bal);
+                    }
+                }
+                if (kf[s] <= kl[s]) {
+                    int iv; float t;
+                    axis_locate(lam[kf[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                    clo = min(clo, fk::first_tap(iv, NW));
+                    axis_locate(lam[kl[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                    chi = max(chi, fk::first_tap(iv, NW) + 3);
+                }
+            }
+        }
+        const int nch = (chi >= clo) ? (chi - clo + WMAXW) / WMAXW : 0;
+
+        double chi_acc[TS];
+        float g[TS][6];
+#pragma unroll
+        for (int s = 0; s < TS; ++s) {
+            chi_acc[s] = 0.0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) g[s][q] = 0.f;
+        }
+        bool bad_obs = false;
+
+        // observation passes: gather this band's observations (in input order)
+        int scan = 0;
+        while (scan < nobs) {
+            int nb_obs = 0;
+            while (scan < nobs && nb_obs < OBS_W) {
+                const int i = scan + lane;
+                int bi = -1;
+                float e = 1.f;
+                if (i < nobs) {
+                    bi = b.band[ob0 + i];
+                    e = b.fluxerr[ob0 + i];
+                    if (bd == 0 && (bi < 0 || bi >= NB || !(e > 0.f))) {
+                        bad_obs = true;
+                        atomicOr(o.err, (bi < 0 || bi >= NB) ? ERRBIT_BAND : ERRBIT_SIGMA);
+                        if (MODE == MODE_BANDFLUX)
+                            for (int s = 0; s < ns; ++s)
+                                o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + s) * nobs + i] = fk::qnanf();
+                    }
+                }
+                const bool mine = i < nobs && bi == bd && e > 0.f;
+                const unsigned bal = __ballot_sync(0xffffffffu, mine);
+                const int room = OBS_W - nb_obs;
+                const int cnt = __popc(bal);
+                const int rank = __popc(bal & ((1u << lane) - 1u));
+                if (mine && rank < room) {
+                    const int slot = nb_obs + rank;
+                    oIdx[slot] = i;
+                    oMjd[slot] = b.mjd[ob0 + i];
+                    oFlux[slot] = b.flux[ob0 + i];
+                    oSig[slot] = e;
+                    oZpf[slot] = zp_scale(b.zp[ob0 + i]);
+                }
+                if (cnt <= room) {
+                    nb_obs += cnt;
+                    scan += 32;
+                } else {
+                    // cache full: resume right after the last observation taken
+                    nb_obs += room;
+                    scan += (int)__fns(bal, 0, room) + 1;
+                    break;
+                }
+            }
+            bad_obs = __any_sync(0xffffffffu, bad_obs);
+            __syncwarp();
+            if (nb_obs == 0) continue;
+
+            // touched phase rows of this pass, compacted into rowl
+            unsigned msk[NPHW / 32] = {0u, 0u, 0u, 0u};
+            for (int base = 0; base < nb_obs; base += 32) {
+                const int il = base + lane;
+                if (il < nb_obs) {
+#pragma unroll
+                    for (int s = 0; s < TS; ++s) {
+                        if (!pok[s]) continue;
+                        const float p = (float)(oMjd[il] - pt0[s]) * pa[s];
+                        int iv; float t;
+                        if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
+                            const int first = fk::first_tap(iv, NP);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) msk[(first + q) >> 5] |= 1u << ((first + q) & 31);
+                        }
+                    }
+                }
+            }
+            int nrows = 0;
+#pragma unroll
+            for (int w = 0; w < NPHW / 32; ++w) {
+                const unsigned word = __reduce_or_sync(0xffffffffu, msk[w]);
+                const bool on = (word >> lane) & 1u;
+                if (on) rowl[nrows + __popc(word & ((1u << lane) - 1u))] = w * 32 + lane;
+                nrows += __popc(word);
+            }
+            __syncwarp();
+            for (int q = lane; q < nrows * TS * ND; q += 32) {
+                const int rr = q / (TS * ND);
+                D[rowl[rr] * TS * ND + (q - rr * TS * ND)] = 0.f;
+            }
+            __syncwarp();
+
+            // column response and forward row dots, per column chunk
+            for (int ch = 0; ch < nch; ++ch) {
+                const int cc = clo + ch * WMAXW;
+                const int W = min(WMAXW, chi - cc + 1);
+                for (int q = lane; q < NE * W * TS; q += 32) {
+                    const int e = q / (W * TS);
+                    E[e * WMAXW * TS + (q - e * W * TS)] = 0.f;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < TS; ++s) {
+                    if (kf[s] > kl[s]) continue;
+                    if (GRAD)
+                        fk::ebuild3(m, lam, wk, kl[s], kf[s], 32, pa[s], pc[s], cc, W, lane, E + s,
+                                    E + WMAXW * TS + s, E + 2 * WMAXW * TS + s, TS);
+                    else
+                        fk::ebuild(m, lam, wk, kl[s], kf[s], 32, pa[s], pc[s], cc, W, lane, E + s, TS);
+                }
+                __syncwarp();
+                const int l4 = lane & 3;
+                for (int rb = 0; rb < nrows; rb += 8) {
+                    const int rr = rb + (lane >> 2);
+                    const bool valid = rr < nrows;
+                    const int r = valid ? rowl[rr] : 0;
+                    float acc[TS][ND];
+#pragma unroll
+                    for (int s = 0; s < TS; ++s)
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) acc[s][d] = 0.f;
+                    if (valid) {
+                        const float2 *grow = m.g01 + (size_t)r * m.nw_pitch + cc;
+                        constexpr int UF = 8;
+                        for (int col0 = l4; col0 < W; col0 += 4 * UF) {
+                            float2 gv[UF];
+#pragma unroll
+                            for (int uu = 0; uu < UF; ++uu) {
+                                const int col = col0 + 4 * uu;
+                                gv[uu] = col < W ? __ldg(grow + col) : make_float2(0.f, 0.f);
+                            }
+#pragma unroll
+                            for (int uu = 0; uu < UF; ++uu) {
+                                const int col = min(col0 + 4 * uu, W - 1);
+#pragma unroll
+                                for (int s = 0; s < TS; ++s)
+#pragma unroll
+                                    for (int e = 0; e < NE; ++e) {
+                                        const float ev = E[e * WMAXW * TS + col * TS + s];
+                                        acc[s][2 * e] = fmaf(gv[uu].x, ev, acc[s][2 * e]);
+                                        acc[s][2 * e + 1] = fmaf(gv[uu].y, ev, acc[s][2 * e + 1]);
+                                    }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < TS; ++s)
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            acc[s][d] += __shfl_xor_sync(0xffffffffu, acc[s][d], 1);
+                            acc[s][d] += __shfl_xor_sync(0xffffffffu, acc[s][d], 2);
+                        }
+                    if (valid && l4 == 0) {
+#pragma unroll
+                        for (int s = 0; s < TS; ++s)
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) D[(r * TS + s) * ND + d] += acc[s][d];
+                    }
+                }
+                __syncwarp();
+            }
+
+            // epilogue per (observation, sample): bandflux, residual, chi^2, gradient terms, adjoint rows
+            for (int base = 0; base < nb_obs; base += 32) {
+                const int il = base + lane;
+                const bool act = il < nb_obs;
+                const double mj = act ? oMjd[il] : 0.0;
+                const float zpf = act ? oZpf[il] : 0.f;
+                const float fl = act ? oFlux[il] : 0.f;
+                const float sig = act ? oSig[il] : 1.f;
+#pragma unroll
+                for (int s = 0; s < TS; ++s) {
+                    Taps4 tp;
+                    float Bs = 0.f, Bp = 0.f, B1 = 0.f, Bc = 0.f, Bz = 0.f;
+                    if (act && s < ns) {
+                        const float a = pa[s];
+                        const float p = (float)(mj - pt0[s]) * a;
+                        int iv; float t;
+                        if (pok[s] && axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
+                            axis_taps_from<GRAD>(iv, t, NP, m.inv_dphase, tp);
+#pragma unroll
+                            for (int mm = 0; mm < 4; ++mm) {
+                                const float *dv = D + ((tp.first + mm) * TS + s) * ND;
+                                const float h = fmaf(px1[s], dv[1], dv[0]);
+                                Bs = fmaf(tp.w[mm], h, Bs);
+                                if (GRAD) {
+                                    Bp = fmaf(tp.dw[mm], h, Bp);
+                                    B1 = fmaf(tp.w[mm], dv[1], B1);
+                                    Bc = fmaf(tp.w[mm], fmaf(px1[s], dv[3], dv[2]), Bc);
+                                    Bz = fmaf(tp.w[mm], fmaf(px1[s], dv[5], dv[4]), Bz);
+                                }
+                            }
+                        }
+                        const float pre = px0[s] * a * zpf;
+                        const float B = pre * Bs;
+                        if (MODE == MODE_BANDFLUX) {
+                            o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + s) * nobs + oIdx[il]] = pok[s] ? B : fk::qnanf();
+                        } else {
+                            const float r = (fl - B) / sig;
+                            chi_acc[s] = fma((double)r, (double)r, chi_acc[s]);
+                            if (GRAD) {
+                                const float gg = -2.0f * r / sig;
+                                g[s][0] += gg * (-a * B - pre * a * p * Bp);
+                                g[s][1] += gg * pre * Bp * (-a);
+                                g[s][2] += gg * a * zpf * Bs;
+                                g[s][3] += gg * pre * B1;
+                                g[s][4] += gg * pre * Bc;
+                                g[s][5] += gg * pre * Bz;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }  // observation passes
+
+        if (MODE == MODE_BANDFLUX) continue;  // bandfluxes are written by the epilogue
+
+        // unit partials -> scratch; the last band of the item combines in band order
+        double *pbase = scr.partial + (size_t)item * TS * NB * NSLOT;
+#pragma unroll
+        for (int s = 0; s < TS; ++s) {
+            const double x2 = warp_sum_d(chi_acc[s]);
+            float gs[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) gs[q] = GRAD ? warp_sum(g[s][q]) : 0.f;
+            if (lane == 0) {
+                double *sl = pbase + ((size_t)s * NB + bd) * NSLOT;
+                sl[0] = x2;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) sl[1 + q] = gs[q];
+                sl[7] = bad_obs ? 1.0 : 0.0;
+            }
+        }
+        int last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = atomicAdd(scr.arrive + item, 1) == NB - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) continue;
+        __threadfence();
+        if (lane < ns) {
+            const int s = lane;
+            double x2 = 0.0;
+            float gg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool badv = false;
+            for (int bb = 0; bb < NB; ++bb) {
+                const double *sl = pbase + ((size_t)s * NB + bb) * NSLOT;
+                x2 += __ldcg(sl);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) gg[q] += (float)__ldcg(sl + 1 + q);
+                badv |= __ldcg(sl + 7) != 0.0;
+            }
+            const bool bad = badv || !pok[min(s, TS - 1)];
+            const int64_t gj = wi.par0 + s;
+            o.chi2[gj] = bad ? __longlong_as_double(0x7ff8000000000000ll) : x2;
+            if (GRAD) {
+                const float gout[5] = {gg[0] + gg[5], gg[1], gg[2], gg[3], gg[4]};
+#pragma unroll
+                for (int q = 0; q < 5; ++q) o.grad[5 * gj + q] = bad ? fk::qnanf() : gout[q];
+            }
+        }
+        if (lane == 0) scr.arrive[item] = 0;  // ready for the next launch
+    }
+}
+
+}  // namespace uk
+
+int unit_item_samples() { return 2; }
+int unit_max_phase() { return uk::NPHW; }
+size_t unit_scratch_bytes(int n_items, int ts, int n_bands) {
+    return (size_t)n_items * ts * (n_bands > 0 ? n_bands : 1) * uk::NSLOT * sizeof(double) +
+           (size_t)n_items * sizeof(int) + 256;
+}
+
+template <int TS, int MODE>
+static cudaError_t launch_uk(const salt_ctx *ctx, const WorkItem *items_d, int n_items, int *counter_d,
+                             void *scratch, const BatchDev &b, const OutDev &o, cudaStream_t st) {
+    const size_t smem = uk::Lay(TS, MODE == MODE_GRAD).total;
+    static std::atomic<int> attr_done[64];
+    cudaError_t e;
+    const int dv = ctx->device & 63;
+    if (!attr_done[dv].load()) {
+        e = cudaFuncSetAttribute(uk::k_unit<TS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[dv].store(1);
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, uk::k_unit<TS, MODE>, uk::THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int nb = ctx->mp.bands.n_bands > 0 ? ctx->mp.bands.n_bands : 1;
+    const int64_t units = (int64_t)n_items * nb;
+    int grid = ctx->num_sms * per_sm;
+    if ((int64_t)grid * uk::WARPS > units) grid = (int)((units + uk::WARPS - 1) / uk::WARPS);
+    if (grid < 1) return cudaSuccess;
+    uk::UnitScratch scr;
+    scr.partial = (double *)scratch;
+    scr.arrive = (int *)((unsigned char *)scratch + (size_t)n_items * TS * nb * uk::NSLOT * sizeof(double));
+    e = cudaMemsetAsync(counter_d, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    uk::k_unit<TS, MODE><<<grid, uk::THREADS, smem, st>>>(ctx->mp, b, o, items_d, n_items, counter_d, scr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_items(const salt_ctx *ctx, int ts, const WorkItem *items_d, int n_items, int *counter_d,
+                              void *scratch, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    if (ts == 2) {
+        switch (mode) {
+            case MODE_BANDFLUX: return launch_uk<2, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+            case MODE_CHI2: return launch_uk<2, MODE_CHI2>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+            default: return launch_uk<2, MODE_GRAD>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+        }
+    }
+    switch (mode) {
+        case MODE_BANDFLUX: return launch_uk<1, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+        case MODE_CHI2: return launch_uk<1, MODE_CHI2>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+        default: return launch_uk<1, MODE_GRAD>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+    }
+}
+
+}  // namespace salt

@@ -84,7 +84,7 @@ struct WorkItem {
 };
 
 // Launch configurations of the factorised path: kernel family and tile.
-enum Family : int { FAM_CTA = 0, FAM_WARP = 1 };
+enum Family : int { FAM_CTA = 0, FAM_WARP = 1, FAM_UNIT = 2 };
 inline int cfg_key(int family, int tile) { return family * 16 + tile; }
 inline int cfg_family(int key) { return key / 16; }
 inline int cfg_tile(int key) { return key % 16; }
@@ -101,6 +101,7 @@ struct salt_plan {
     struct ItemList {
         salt::WorkItem *d = nullptr;
         int n = 0;
+        void *scratch = nullptr;  // per-item partials + arrival counters (warp-unit family)
     };
     std::map<int, ItemList> lists;
     int choice[3] = {-1, -1, -1};  // tuned configuration key per mode (-1 = not tuned yet)
@@ -149,6 +150,10 @@ cudaError_t launch_bandwarp_items(const salt_ctx *ctx, int ts, const WorkItem *i
                                   cudaStream_t st);
 int bandwarp_item_samples();
 int bandwarp_max_phase();
+cudaError_t launch_unit_items(const salt_ctx *ctx, int ts, const WorkItem *items_d, int n_items, int *counter_d,
+                              void *scratch, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st);
+int unit_max_phase();
+size_t unit_scratch_bytes(int n_items, int ts, int n_bands);
 cudaError_t launch_validate(const salt_ctx *ctx, const BatchDev &b, int *flag, cudaStream_t st);
 int factorised_smem_bytes(int tile, int mode);
 int factorised_max_tile();

@@ -14,7 +14,7 @@ from tests import _helpers as H
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-KERNELS = {"direct": 1, "factorised": 2, "bandwarp": 3, "auto": 0}
+KERNELS = {"direct": 1, "factorised": 2, "bandwarp": 3, "unit": 4, "auto": 0}
 
 
 def _salt(wl, **kw):
@@ -64,7 +64,7 @@ def test_bandflux_single_supernova(cfg1, kernel):
     s.check()
 
 
-@pytest.mark.parametrize("kernel", ["direct", "factorised", "bandwarp"])
+@pytest.mark.parametrize("kernel", ["direct", "factorised", "bandwarp", "unit"])
 @pytest.mark.parametrize("tile", [1, 2, 4, 8])
 def test_bandflux_and_chi2_batched(cfg2_sub, kernel, tile):
     wl, o = cfg2_sub
@@ -81,7 +81,7 @@ def test_bandflux_and_chi2_batched(cfg2_sub, kernel, tile):
     s.check()
 
 
-@pytest.mark.parametrize("kernel", ["direct", "factorised", "bandwarp", "auto"])
+@pytest.mark.parametrize("kernel", ["direct", "factorised", "bandwarp", "unit", "auto"])
 @pytest.mark.parametrize("tile", [1, 2, 8])
 def test_chi2_grad_many_samples(cfg3_sub, kernel, tile):
     wl, o = cfg3_sub
