@@ -231,6 +231,38 @@ typedef struct {
 
 int salt_serve_stats_get(salt_ctx *ctx, salt_serve_stats *out);
 
+/* ------------------------------------------------- no-allocation variant - */
+
+/* Bytes of device scratch available to salt_chi2_grad_noalloc: one fixed
+ * array inside the library per device (held from module load on). */
+#define SALT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* salt_chi2_grad without any device-memory allocation during the call. The
+ * paper has no counterpart: it is a service for callers that cannot allocate,
+ * e.g. a process whose device memory is all reserved by another allocator's
+ * pool (a caching allocator that has taken the free HBM), or a fitting loop
+ * that cannot afford the stalls of allocation (cudaFree synchronises the
+ * device). Same arguments, outputs (chi2: DEVICE float64 [n_par]; grad:
+ * DEVICE float32 [n_par][5]) and data errors as salt_chi2_grad; it always
+ * runs the warp-unit kernel with one sample per unit (SALT_KERNEL_UNIT,
+ * tile 1) and ignores batch->plan and the kernel options.
+ * Scratch: the offset copies, the work list, the unit counter and the
+ * per-band partials come from the library's fixed array; the call needs
+ * 256 + 2 x round256(8 (n_sn + 1)) + round256(40 n_par)
+ *   + 64 n_bands n_par + 4 n_par + 256 bytes
+ * (about 39,000 samples with 6 bands) and returns SALT_ERR_INVALID, touching
+ * nothing, if that exceeds SALT_NOALLOC_SCRATCH_BYTES or if the model has more
+ * than 128 phase nodes; salt_last_error gives the bytes needed. Each call
+ * copies the HOST offsets into the array and clears the counters that must
+ * start at zero, on cuda_stream.
+ * The first call on each device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The array is shared by every call on that device in the process: two calls
+ * whose executions overlap (different streams, threads or contexts on the same
+ * device) race on it and give wrong results, so serialise them. */
+int salt_chi2_grad_noalloc(salt_ctx *ctx, const salt_batch *batch, double *chi2, float *grad,
+                           void *cuda_stream);
+
 /* ---------------------------------------------------------------- misc ---- */
 
 const char *salt_status_str(int status);

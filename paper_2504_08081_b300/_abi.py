@@ -41,7 +41,11 @@ EXPORTS = [
     "salt_bandflux_offsets", "salt_bandflux", "salt_chi2", "salt_chi2_grad", "salt_check",
     "salt_set_option", "salt_get_option", "salt_serve_submit", "salt_serve_poll",
     "salt_serve_cancel", "salt_serve_stats_get", "salt_status_str", "salt_last_error",
+    "salt_chi2_grad_noalloc",
 ]
+
+# Scratch bytes of the no-allocation call (SALT_NOALLOC_SCRATCH_BYTES).
+SALT_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class SaltError(RuntimeError):
@@ -109,6 +113,7 @@ def lib():
     L.salt_bandflux.argtypes = [p, C.POINTER(BatchDesc), p, p]
     L.salt_chi2.argtypes = [p, C.POINTER(BatchDesc), p, p]
     L.salt_chi2_grad.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
+    L.salt_chi2_grad_noalloc.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
     L.salt_check.argtypes = [p, p]
     L.salt_set_option.argtypes = [p, i32, i64]
     L.salt_get_option.argtypes = [p, i32, C.POINTER(i64)]

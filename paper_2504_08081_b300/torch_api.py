@@ -117,6 +117,19 @@ class Salt:
                                                  grad.data_ptr(), _stream(self.device)))
         return chi2, grad
 
+    def chi2_grad_noalloc(self, db: DeviceBatch, chi2: torch.Tensor, grad: torch.Tensor,
+                          validate=False):
+        """chi2_grad through the no-allocation entry point, into caller-owned
+        outputs (float64 [n_par], float32 [n_par, 5] on this device)."""
+        if chi2.dtype != torch.float64 or grad.dtype != torch.float32 or \
+                chi2.numel() < db.n_par or grad.numel() < 5 * db.n_par or \
+                not chi2.is_contiguous() or not grad.is_contiguous():
+            raise ValueError("chi2/grad: contiguous float64 [n_par] / float32 [n_par, 5] tensors")
+        d = self._desc(db, validate)
+        self.ctx.check(_abi.lib().salt_chi2_grad_noalloc(self.ctx.h, C.byref(d), chi2.data_ptr(),
+                                                         grad.data_ptr(), _stream(self.device)))
+        return chi2, grad
+
     def check(self):
         """Synchronise and raise if a kernel met invalid batch data."""
         self.ctx.check(self.ctx.device_check(_stream(self.device)))
