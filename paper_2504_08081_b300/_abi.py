@@ -28,6 +28,7 @@ SALT_OPT_KERNEL = 1
 SALT_OPT_TILE_SAMPLES = 2
 SALT_OPT_GRAPHS = 3
 SALT_OPT_SERVE_CHUNK = 4
+SALT_OPT_LAST_KERNEL = 5
 
 SALT_KERNEL_AUTO = 0
 SALT_KERNEL_DIRECT = 1

@@ -207,6 +207,7 @@ extern "C" void salt_destroy(salt_ctx *ctx) {
     if (ctx->band_lam_d) cudaFree(ctx->band_lam_d);
     if (ctx->band_w_d) cudaFree(ctx->band_w_d);
     if (ctx->err_d) cudaFree(ctx->err_d);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
     cudaSetDevice(prev);
     (void)cudaGetLastError();
@@ -440,10 +441,63 @@ static int tune(salt_ctx *ctx, salt_plan *p, const BatchDev &b, const OutDev &o,
     return SALT_OK;
 }
 
+// Graph replay for repeated plan calls. A call whose batch and output pointers
+// equal the previous call's (same mode and configuration) is captured once on
+// the context's private stream (the launch's counter reset and kernel become a
+// two-node graph) and replayed on the caller's stream from then on; a call with
+// new pointers launches directly and drops the stale graph. Returns false when
+// the caller should launch directly (never while the caller's stream is
+// capturing: the caller's own graph then records the direct launch).
+static bool replay_graph(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b, const OutDev &o, int mode,
+                         cudaStream_t st, cudaError_t *err) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    salt_plan::GraphEntry &G = p->graphs[mode * 256 + key];
+    if (G.failed) return false;
+    const bool same = G.seen && std::memcmp(&G.b, &b, sizeof b) == 0 && std::memcmp(&G.o, &o, sizeof o) == 0;
+    if (!same) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+        G.b = b;
+        G.o = o;
+        G.seen = true;
+        return false;
+    }
+    if (!G.exec) {
+        if (!ctx->capture_stream &&
+            cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            G.failed = true;
+            return false;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t el = launch_key(ctx, p, key, b, o, mode, ctx->capture_stream);
+            e = cudaStreamEndCapture(ctx->capture_stream, &g);
+            if (el != cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            G.exec = nullptr;
+            G.failed = true;
+            return false;
+        }
+    }
+    *err = cudaGraphLaunch(G.exec, st);
+    return true;
+}
+
 int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const OutDev &o, int mode,
               cudaStream_t st) {
     salt_plan *p = const_cast<salt_plan *>(cplan);  // tuning state and work lists are a cache
     if (ctx->kernel == SALT_KERNEL_DIRECT) {
+        ctx->last_kernel = SALT_KERNEL_DIRECT * 16;
         cudaError_t e = launch_direct(ctx, b, o, mode, st);
         return e == cudaSuccess ? SALT_OK : cuda_err(ctx, e, "kernel launch");
     }
@@ -490,7 +544,14 @@ int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const Ou
     }
     int rc = build_items(ctx, p, key, st);
     if (rc != SALT_OK) return rc;
-    cudaError_t e = launch_key(ctx, p, key, b, o, mode, st);
+    const int fam = cfg_family(key);
+    ctx->last_kernel = (fam == FAM_UNIT ? SALT_KERNEL_UNIT : fam == FAM_WARP ? SALT_KERNEL_BANDWARP
+                                                                             : SALT_KERNEL_FACTORISED) * 16 +
+                       cfg_tile(key);
+    cudaError_t e;
+    if (ctx->use_graphs && !p->temporary && replay_graph(ctx, p, key, b, o, mode, st, &e))
+        return e == cudaSuccess ? SALT_OK : cuda_err(ctx, e, "graph launch");
+    e = launch_key(ctx, p, key, b, o, mode, st);
     if (e != cudaSuccess) return cuda_err(ctx, e, "kernel launch");
     return SALT_OK;
 }
@@ -662,6 +723,7 @@ extern "C" int salt_get_option(const salt_ctx *ctx, int32_t option, int64_t *val
         case SALT_OPT_TILE_SAMPLES: *value = ctx->tile_samples; return SALT_OK;
         case SALT_OPT_GRAPHS: *value = ctx->use_graphs; return SALT_OK;
         case SALT_OPT_SERVE_CHUNK: *value = ctx->serve_chunk; return SALT_OK;
+        case SALT_OPT_LAST_KERNEL: *value = ctx->last_kernel; return SALT_OK;
     }
     return SALT_ERR_INVALID;
 }

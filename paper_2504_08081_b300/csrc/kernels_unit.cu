@@ -21,18 +21,17 @@ constexpr int WARPS = THREADS / 32;
 constexpr int OBS_W = 128;  // observations of the unit's band cached per pass
 constexpr int WMAXW = 192;  // window columns per chunk
 constexpr int NPHW = 128;   // phase nodes supported by this kernel
-constexpr int KTOT = 2048;  // band samples (all bands) staged in shared memory per CTA
 constexpr int NSLOT = 8;    // doubles per (sample, band) partial: chi2, g[6], invalid flag
 
 using fk::al16;
 
 struct Lay {
-    size_t lam, wk, warp0, warp_bytes, total;
+    // No block-level staging: the band tables are read through L1, which keeps
+    // the per-block footprint at three resident blocks per SM.
+    size_t warp0, warp_bytes, total;
     __host__ __device__ Lay(int ts, bool grad) {
         const int ne = grad ? 3 : 1;
         size_t o = 0;
-        lam = o; o = al16(o + 4 * KTOT);
-        wk = o;  o = al16(o + 4 * KTOT);
         warp0 = o;
         // per warp: obs cache (index, mjd, flux, sig, zpf), E (and E_c, E_z) [WMAXW][ts],
         // row dots D [NPHW][ts][2 ne], row list [NPHW]
@@ -59,16 +58,6 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     const Lay L(TS, GRAD);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int NB = m.bands.n_bands, NW = m.n_wave, NP = m.n_phase;
-    float *sLam = (float *)(smem + L.lam);
-    float *sWk = (float *)(smem + L.wk);
-    const bool bands_staged = m.bands.k_total <= KTOT;
-    if (bands_staged)
-        for (int k = tid; k < m.bands.k_total; k += THREADS) {
-            sLam[k] = __ldg(m.band_lam + k);
-            sWk[k] = __ldg(m.band_w + k);
-        }
-    __syncthreads();  // the only block barrier: band samples staged
-
     unsigned char *wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
     int *oIdx = (int *)wb;                                     wb += al16(4 * OBS_W);
     double *oMjd = (double *)wb;                               wb += al16(8 * OBS_W);
@@ -108,8 +97,8 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             }
         }
         const int K = m.bands.n[bd], koff = m.bands.off[bd];
-        const float *lam = (bands_staged ? sLam : m.band_lam) + koff;
-        const float *wk = (bands_staged ? sWk : m.band_w) + koff;
+        const float *lam = m.band_lam + koff;
+        const float *wk = m.band_w + koff;
 
         // in-grid band-sample range per sample (contiguous in k) and the union window
         int kf[TS], kl[TS];

@@ -107,11 +107,17 @@ struct salt_plan {
     int choice[3] = {-1, -1, -1};  // tuned configuration key per mode (-1 = not tuned yet)
     int *counter_d = nullptr;      // dynamic work counter of the persistent kernels
     bool temporary = false;
-    // captured CUDA graphs keyed by the launch signature
+    // Captured CUDA graphs, one per (mode, launch configuration): the batch and
+    // output pointers of the last direct launch, and the graph captured once
+    // the same pointers came back.
     struct GraphEntry {
+        salt::BatchDev b{};
+        salt::OutDev o{};
+        bool seen = false;     // b/o hold the last call's pointers
+        bool failed = false;   // capture failed once: launch directly from then on
         cudaGraphExec_t exec = nullptr;
     };
-    std::map<std::string, GraphEntry> graphs;
+    std::map<int, GraphEntry> graphs;
 };
 
 namespace salt {
@@ -130,6 +136,8 @@ struct salt_ctx {
     int tile_samples = 0;  // 0 = autotuned
     int use_graphs = 1;
     int serve_chunk = 64;
+    int last_kernel = 0;   // SALT_KERNEL_* x 16 + tile of the last batch launch (0 = none yet)
+    cudaStream_t capture_stream = nullptr;  // private stream for graph capture (created on first use)
     std::vector<double> host_cl;  // colour-law coefficients (for serving validation)
     salt::ServeEngine *serve = nullptr;
     size_t serve_mem = 0;

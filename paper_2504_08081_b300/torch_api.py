@@ -140,6 +140,14 @@ class Salt:
     def set_tile(self, tile: int):
         self.ctx.set_option(_abi.SALT_OPT_TILE_SAMPLES, tile)
 
+    def set_graphs(self, on: bool):
+        self.ctx.set_option(_abi.SALT_OPT_GRAPHS, 1 if on else 0)
+
+    def last_kernel(self) -> tuple[int, int]:
+        """(SALT_KERNEL_* family, samples per tile) of the last batch launch."""
+        v = self.ctx.get_option(_abi.SALT_OPT_LAST_KERNEL)
+        return v // 16, v % 16
+
     # -- serving -------------------------------------------------------------
     def submit(self, n_obs, mjd, band, flux, fluxerr, zp, t0, z, x0, x1, c, want_grad) -> int:
         arrs = [np.ascontiguousarray(mjd, np.float64), np.ascontiguousarray(band, np.int32),
