@@ -48,24 +48,27 @@ __device__ __forceinline__ bool axis_locate(float x, float x0, float inv_dx, flo
 }
 
 // Weights (and optionally derivatives w.r.t. x) for a located interval.
+// Written with selects only (no runtime index into the tap arrays), so the
+// taps stay in registers.
 template <bool DERIV>
 __device__ __forceinline__ void axis_taps_from(int i, float t, int n, float inv_dx, Taps4 &tp) {
-    if (i == 0 || i == n - 2) {
-        tp.first = (i == 0) ? 0 : n - 4;
-        int o = (i == 0) ? 0 : 2;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) { tp.w[m] = 0.f; if (DERIV) tp.dw[m] = 0.f; }
-        tp.w[o] = 1.0f - t;
-        tp.w[o + 1] = t;
-        if (DERIV) { tp.dw[o] = -inv_dx; tp.dw[o + 1] = inv_dx; }
-    } else {
-        tp.first = i - 1;
-        keys_weights(t, tp.w);
-        if (DERIV) {
-            keys_dweights(t, tp.dw);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) tp.dw[m] *= inv_dx;
-        }
+    const bool edge = i == 0 || i == n - 2;
+    const bool lo = i == 0;  // first interval: linear weights on nodes 0, 1; last: on n-2, n-1
+    tp.first = edge ? (lo ? 0 : n - 4) : i - 1;
+    float kw[4];
+    keys_weights(t, kw);
+    const float l0 = 1.0f - t;
+    tp.w[0] = edge ? (lo ? l0 : 0.f) : kw[0];
+    tp.w[1] = edge ? (lo ? t : 0.f) : kw[1];
+    tp.w[2] = edge ? (lo ? 0.f : l0) : kw[2];
+    tp.w[3] = edge ? (lo ? 0.f : t) : kw[3];
+    if (DERIV) {
+        float kd[4];
+        keys_dweights(t, kd);
+        tp.dw[0] = edge ? (lo ? -inv_dx : 0.f) : kd[0] * inv_dx;
+        tp.dw[1] = edge ? (lo ? inv_dx : 0.f) : kd[1] * inv_dx;
+        tp.dw[2] = edge ? (lo ? 0.f : -inv_dx) : kd[2] * inv_dx;
+        tp.dw[3] = edge ? (lo ? 0.f : inv_dx) : kd[3] * inv_dx;
     }
 }
 

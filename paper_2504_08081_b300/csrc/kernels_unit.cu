@@ -19,7 +19,7 @@ namespace uk {
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int OBS_W = 128;  // observations of the unit's band cached per pass
-constexpr int WMAXW = 192;  // window columns per chunk
+constexpr int WMAXW = 160;  // window columns per chunk
 constexpr int NPHW = 128;   // phase nodes supported by this kernel
 constexpr int NSLOT = 8;    // doubles per (sample, band) partial: chi2, g[6], invalid flag
 
@@ -33,10 +33,11 @@ struct Lay {
         const int ne = grad ? 3 : 1;
         size_t o = 0;
         warp0 = o;
-        // per warp: obs cache (index, mjd, flux, sig, zpf), E (and E_c, E_z) [WMAXW][ts],
-        // row dots D [NPHW][ts][2 ne], row list [NPHW]
-        warp_bytes = al16(4 * OBS_W) + al16(8 * OBS_W) + 3 * al16(4 * OBS_W) + al16(4 * (size_t)WMAXW * ts * ne) +
-                     al16(4 * (size_t)NPHW * ts * 2 * ne) + al16(4 * NPHW);
+        // per warp: obs cache (index, mjd, flux, sig, zpf), column responses
+        // [WMAXW][ts][E (, E_c, E_z, pad)], row dots D [NPHW][ts][2 ne], row list [NPHW]
+        warp_bytes = al16(4 * OBS_W) + al16(8 * OBS_W) + 3 * al16(4 * OBS_W) +
+                     al16(4 * (size_t)WMAXW * ts * (grad ? 4 : 1)) + al16(4 * (size_t)NPHW * ts * 2 * ne) +
+                     al16(4 * NPHW);
         o += WARPS * warp_bytes;
         total = o;
     }
@@ -47,6 +48,28 @@ struct UnitScratch {
     int *arrive;      // [n_items] bands finished (reset by the combining warp)
 };
 
+// Sums of 8 per-lane values over the warp by reduce-scatter (9 shuffles instead
+// of 40): lane L returns the total of value (L >> 2) & 7. Fixed order.
+__device__ __forceinline__ float warp_sum8_scatter(const float (&v)[8], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float k4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float r = __shfl_xor_sync(0xffffffffu, h16 ? v[j] : v[j + 4], 16);
+        k4[j] = (h16 ? v[j + 4] : v[j]) + r;
+    }
+    float k2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float r = __shfl_xor_sync(0xffffffffu, h8 ? k4[j] : k4[j + 2], 8);
+        k2[j] = (h8 ? k4[j + 2] : k4[j]) + r;
+    }
+    float k1 = (h4 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? k2[0] : k2[1], 4);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+    return k1;
+}
+
 template <int TS, int MODE>
 __global__ void __launch_bounds__(THREADS, 3)
 k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items, int *counter,
@@ -54,6 +77,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     constexpr bool GRAD = MODE == MODE_GRAD;
     constexpr int NE = GRAD ? 3 : 1;  // column responses per sample: E (, E_c, E_z)
     constexpr int ND = 2 * NE;        // row dots per (row, sample): x surfaces M0, M1
+    constexpr int NEP = GRAD ? 4 : 1; // column-response slots per (column, sample)
     extern __shared__ __align__(16) unsigned char smem[];
     const Lay L(TS, GRAD);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -64,12 +88,14 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *oFlux = (float *)wb;                                wb += al16(4 * OBS_W);
     float *oSig = (float *)wb;                                 wb += al16(4 * OBS_W);
     float *oZpf = (float *)wb;                                 wb += al16(4 * OBS_W);
-    float *E = (float *)wb;                                    wb += al16(4 * (size_t)WMAXW * TS * NE);
+    float *E = (float *)wb;                                    wb += al16(4 * (size_t)WMAXW * TS * NEP);
     float *D = (float *)wb;                                    wb += al16(4 * (size_t)NPHW * TS * ND);
     int *rowl = (int *)wb;
 
     const int n_units = n_items * NB;
     for (;;) {
+        // claim one unit at a time: with few units per warp, claiming ahead
+        // would fix the assignment and undo the dynamic balancing
         int u = 0;
         if (lane == 0) u = atomicAdd(counter, 1);
         u = __shfl_sync(0xffffffffu, u, 0);
@@ -106,7 +132,10 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
 #pragma unroll
         for (int s = 0; s < TS; ++s) {
             kf[s] = K; kl[s] = -1;
-            if (pok[s]) {
+            if (pok[s] && K > 0 && lam[0] * pa[s] >= m.wave0 && lam[K - 1] * pa[s] <= m.wave_max) {
+                kf[s] = 0;  // lambda ascending: both ends inside means every sample is
+                kl[s] = K - 1;
+            } else if (pok[s]) {
                 for (int k0 = 0; k0 < K; k0 += 32) {
                     const int k = k0 + lane;
                     bool in = false;
@@ -120,13 +149,13 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         kl[s] = k0 + 31 - __clz(bal);
                     }
                 }
-                if (kf[s] <= kl[s]) {
-                    int iv; float t;
-                    axis_locate(lam[kf[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
-                    clo = min(clo, fk::first_tap(iv, NW));
-                    axis_locate(lam[kl[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
-                    chi = max(chi, fk::first_tap(iv, NW) + 3);
-                }
+            }
+            if (kf[s] <= kl[s]) {
+                int iv; float t;
+                axis_locate(lam[kf[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                clo = min(clo, fk::first_tap(iv, NW));
+                axis_locate(lam[kl[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                chi = max(chi, fk::first_tap(iv, NW) + 3);
             }
         }
         const int nch = (chi >= clo) ? (chi - clo + WMAXW) / WMAXW : 0;
@@ -145,13 +174,32 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
         int scan = 0;
         while (scan < nobs) {
             int nb_obs = 0;
+            // band ids and errors of the next PRE chunks of 32, loaded together so
+            // that their latencies overlap
+            constexpr int PRE = 8;
+            int pb[PRE];
+            float pe[PRE];
+            const int base0 = scan;
+#pragma unroll
+            for (int j = 0; j < PRE; ++j) {
+                const int i = base0 + 32 * j + lane;
+                pb[j] = i < nobs ? __ldg(b.band + ob0 + i) : -1;
+                pe[j] = i < nobs ? __ldg(b.fluxerr + ob0 + i) : 1.f;
+            }
             while (scan < nobs && nb_obs < OBS_W) {
                 const int i = scan + lane;
                 int bi = -1;
                 float e = 1.f;
                 if (i < nobs) {
-                    bi = b.band[ob0 + i];
-                    e = b.fluxerr[ob0 + i];
+                    const int off = scan - base0;  // warp-uniform
+                    if ((off & 31) == 0 && off < 32 * PRE) {
+#pragma unroll
+                        for (int j = 0; j < PRE; ++j)
+                            if (off == 32 * j) { bi = pb[j]; e = pe[j]; }
+                    } else {
+                        bi = b.band[ob0 + i];
+                        e = b.fluxerr[ob0 + i];
+                    }
                     if (bd == 0 && (bi < 0 || bi >= NB || !(e > 0.f))) {
                         bad_obs = true;
                         atomicOr(o.err, (bi < 0 || bi >= NB) ? ERRBIT_BAND : ERRBIT_SIGMA);
@@ -199,8 +247,14 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         int iv; float t;
                         if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
                             const int first = fk::first_tap(iv, NP);
+                            const int w0 = first >> 5, sh = first & 31;
+                            const unsigned lo = 0xfu << sh;                       // rows in word w0
+                            const unsigned hi = sh > 28 ? 0xfu >> (32 - sh) : 0u;  // rows in word w0 + 1
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) msk[(first + q) >> 5] |= 1u << ((first + q) & 31);
+                            for (int w = 0; w < NPHW / 32; ++w) {  // registers only: no dynamic index
+                                if (w == w0) msk[w] |= lo;
+                                if (w == w0 + 1) msk[w] |= hi;
+                            }
                         }
                     }
                 }
@@ -224,17 +278,14 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             for (int ch = 0; ch < nch; ++ch) {
                 const int cc = clo + ch * WMAXW;
                 const int W = min(WMAXW, chi - cc + 1);
-                for (int q = lane; q < NE * W * TS; q += 32) {
-                    const int e = q / (W * TS);
-                    E[e * WMAXW * TS + (q - e * W * TS)] = 0.f;
-                }
+                for (int q = lane; q < W * TS * NEP; q += 32) E[q] = 0.f;
                 __syncwarp();
 #pragma unroll
                 for (int s = 0; s < TS; ++s) {
                     if (kf[s] > kl[s]) continue;
                     if (GRAD)
-                        fk::ebuild3(m, lam, wk, kl[s], kf[s], 32, pa[s], pc[s], cc, W, lane, E + s,
-                                    E + WMAXW * TS + s, E + 2 * WMAXW * TS + s, TS);
+                        fk::ebuild3(m, lam, wk, kl[s], kf[s], 32, pa[s], pc[s], cc, W, lane, E + 4 * s,
+                                    E + 4 * s + 1, E + 4 * s + 2, 4 * TS);
                     else
                         fk::ebuild(m, lam, wk, kl[s], kf[s], 32, pa[s], pc[s], cc, W, lane, E + s, TS);
                 }
@@ -263,13 +314,21 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             for (int uu = 0; uu < UF; ++uu) {
                                 const int col = min(col0 + 4 * uu, W - 1);
 #pragma unroll
-                                for (int s = 0; s < TS; ++s)
-#pragma unroll
-                                    for (int e = 0; e < NE; ++e) {
-                                        const float ev = E[e * WMAXW * TS + col * TS + s];
-                                        acc[s][2 * e] = fmaf(gv[uu].x, ev, acc[s][2 * e]);
-                                        acc[s][2 * e + 1] = fmaf(gv[uu].y, ev, acc[s][2 * e + 1]);
+                                for (int s = 0; s < TS; ++s) {
+                                    if constexpr (GRAD) {
+                                        const float4 ev = *reinterpret_cast<const float4 *>(E + (col * TS + s) * 4);
+                                        acc[s][0] = fmaf(gv[uu].x, ev.x, acc[s][0]);
+                                        acc[s][1] = fmaf(gv[uu].y, ev.x, acc[s][1]);
+                                        acc[s][2] = fmaf(gv[uu].x, ev.y, acc[s][2]);
+                                        acc[s][3] = fmaf(gv[uu].y, ev.y, acc[s][3]);
+                                        acc[s][4] = fmaf(gv[uu].x, ev.z, acc[s][4]);
+                                        acc[s][5] = fmaf(gv[uu].y, ev.z, acc[s][5]);
+                                    } else {
+                                        const float ev = E[col * TS + s];
+                                        acc[s][0] = fmaf(gv[uu].x, ev, acc[s][0]);
+                                        acc[s][1] = fmaf(gv[uu].y, ev, acc[s][1]);
                                     }
+                                }
                             }
                         }
                     }
@@ -351,15 +410,16 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
 #pragma unroll
         for (int s = 0; s < TS; ++s) {
             const double x2 = warp_sum_d(chi_acc[s]);
-            float gs[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) gs[q] = GRAD ? warp_sum(g[s][q]) : 0.f;
+            double *sl = pbase + ((size_t)s * NB + bd) * NSLOT;
             if (lane == 0) {
-                double *sl = pbase + ((size_t)s * NB + bd) * NSLOT;
                 sl[0] = x2;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) sl[1 + q] = gs[q];
                 sl[7] = bad_obs ? 1.0 : 0.0;
+            }
+            if (GRAD) {
+                float v[8] = {g[s][0], g[s][1], g[s][2], g[s][3], g[s][4], g[s][5], 0.f, 0.f};
+                const float gsum = warp_sum8_scatter(v, lane);
+                const int q = (lane >> 2) & 7;
+                if ((lane & 3) == 0 && q < 6) sl[1 + q] = gsum;
             }
         }
         int last = 0;
@@ -378,8 +438,9 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             for (int bb = 0; bb < NB; ++bb) {
                 const double *sl = pbase + ((size_t)s * NB + bb) * NSLOT;
                 x2 += __ldcg(sl);
+                if (GRAD)
 #pragma unroll
-                for (int q = 0; q < 6; ++q) gg[q] += (float)__ldcg(sl + 1 + q);
+                    for (int q = 0; q < 6; ++q) gg[q] += (float)__ldcg(sl + 1 + q);
                 badv |= __ldcg(sl + 7) != 0.0;
             }
             const bool bad = badv || !pok[min(s, TS - 1)];
