@@ -392,8 +392,10 @@ def run_ours(args, rank, world, local_rank):
     max_mhz = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
     fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the max SM clock
     achieved = flops / (ms / 1e3) / 1e12
+    kname = KERNEL_NAMES[fam].format(tile)
+    traffic, traffic_src = measured_traffic(kname, W.CONFIG_NAMES[args.workload])
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": KERNEL_NAMES[fam].format(tile),
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "flop_per_launch": flops}
@@ -433,6 +435,27 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu capture summary, or None when there is none or the kernel's
+    sources have changed since it was taken."""
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None, "no capture"
+    if not rec or rec.get("workload") != workload:
+        return None, "no capture of this kernel on this workload"
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in rec["sources"]:
+        h.update(open(os.path.join(root, f), "rb").read())
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None, "kernel changed since the ncu capture"
+    return rec["dram_read_bytes"] + rec["dram_write_bytes"], rec["summary"]
 
 
 def cpu_baseline(wl, budget_s):
