@@ -236,6 +236,20 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- our arm
 
+def reduce_over_ranks(ms, n_bandflux, n_par, device):
+    """Whole-job figures over the ranks of the default process group (if any):
+    the slowest rank's time per step and the summed work of all ranks. Each
+    rank owns its own supernovae; nothing else is exchanged."""
+    import torch
+    import torch.distributed as dist
+    ms_t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    cnt = torch.tensor([float(n_bandflux), float(n_par)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    return float(ms_t.item()), float(cnt[0].item()), float(cnt[1].item())
+
+
 def time_steps(fn, steps, warmup, stream, flush=None, queue_ahead=True):
     """Device time of each step: a pair of CUDA events on `stream` around it,
     the L2 flush (if any) enqueued before the first event. With queue_ahead
@@ -340,13 +354,7 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.destroy_process_group()
         return
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    nbf_t = torch.tensor([float(bt.n_bandflux()), float(bt.n_par)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(nbf_t, op=dist.ReduceOp.SUM)
-    ms_max = float(ms_t.item())
-    n_bf_all, n_par_all = float(nbf_t[0].item()), float(nbf_t[1].item())
+    ms_max, n_bf_all, n_par_all = reduce_over_ranks(ms, bt.n_bandflux(), bt.n_par, dev)
     value = n_bf_all / (ms_max / 1e3)
 
     # ---- end to end through the public API: pinned host inputs -> device -> host results
@@ -371,10 +379,8 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         e2e_durs = time_steps(e2e_step, args.steps, max(args.warmup, 3), stream, flush=flush_buf.zero_)
     e2e_ms = statistics.mean(e2e_durs)
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = n_bf_all / (float(e2e_t.item()) / 1e3)
+    e2e_max, _, _ = reduce_over_ranks(e2e_ms, 0, 0, dev)
+    e2e_value = n_bf_all / (e2e_max / 1e3)
     np.testing.assert_array_equal(chi2_h.numpy(), chi2.cpu().numpy())
 
     if rank != 0:
