@@ -235,6 +235,60 @@ typedef struct {
 
 int salt_serve_stats_get(salt_ctx *ctx, salt_serve_stats *out);
 
+/* ---------------------------------------------------------------- fitting - */
+
+/* Parameters a fit may move (bit i = gradient component i). */
+#define SALT_FIT_Z 1
+#define SALT_FIT_T0 2
+#define SALT_FIT_X0 4
+#define SALT_FIT_X1 8
+#define SALT_FIT_C 16
+#define SALT_FIT_DEFAULT_MASK (SALT_FIT_T0 | SALT_FIT_X0 | SALT_FIT_X1 | SALT_FIT_C)
+
+/* Per-supernova fit outcome (status[s] >= 0: converged after that many
+ * accepted steps). */
+#define SALT_FIT_MAXITER (-1)    /* max_iter steps or max_evals evaluations used */
+#define SALT_FIT_LINESEARCH (-2) /* no step lowers chi^2 any more (at the precision floor) */
+#define SALT_FIT_INVALID (-3)    /* non-finite chi^2 at the start, or an empty box */
+
+/* Options of salt_fit; zero fields take the defaults. */
+typedef struct {
+    int32_t max_iter;   /* accepted steps per fit (default 300) */
+    int32_t max_evals;  /* chi^2 evaluations per fit (default 2 x max_iter + 20) */
+    int32_t history;    /* L-BFGS memory, 1..8 pairs (default 6) */
+    int32_t free_mask;  /* SALT_FIT_* bits of the fitted parameters (default t0, x0, x1, c) */
+    double gtol;        /* stop when the inf-norm of the projected gradient in scaled
+                           variables is <= gtol (default 1e-3) */
+    double ftol;        /* or when an accepted step lowers chi^2 by <= ftol relative
+                           (default 1e-10) */
+} salt_fit_opts;
+
+/* Fit the SALT parameters of every supernova of a batch independently by
+ * minimising its chi^2 (the paper's L-BFGS-B optimisation of x0, x1, t0 and c,
+ * Implementation, first paragraph), all supernovae in lockstep on the device.
+ * Method: bound-constrained limited-memory BFGS in scaled variables
+ * (z/0.01, t0/1 d, x0/|x0 start|, x1, c/0.1): two-loop direction over the
+ * variables not pinned at a bound, steps capped at the box, a strong Wolfe
+ * line search (c1 = 1e-4, c2 = 0.9; bracketing and cubic zoom); each
+ * evaluation is one batched salt_chi2_grad-equivalent pass over every
+ * supernova's trial point.
+ *   batch: exactly one parameter sample per supernova (par_off[s] = s); the
+ *     parameter arrays hold the starting point; validate is ignored.
+ *   lower, upper: DEVICE float64 [n_sn][5] (z, t0, x0, x1, c) box, or NULL for
+ *     unbounded; parameters outside free_mask stay at their start values; a
+ *     free z is kept >= -0.99.
+ *   theta: DEVICE float64 [n_sn][5] out, the best point found (FP32-rounded
+ *     values for z, x0, x1, c: the values the chi^2 was evaluated at);
+ *   chi2: DEVICE float64 [n_sn] out, chi^2 at theta; status: DEVICE int32
+ *     [n_sn] out (>= 0 or SALT_FIT_*).
+ * Synchronises cuda_stream (the host checks progress every 8 iterations).
+ * Allocates its scratch (about 1.2 KB per supernova) for the call.
+ * Returns SALT_ERR_INVALID for bad arguments, SALT_ERR_CUDA/OOM on device
+ * failures. */
+int salt_fit(salt_ctx *ctx, const salt_batch *batch, const double *lower, const double *upper,
+             const salt_fit_opts *opts, double *theta, double *chi2, int32_t *status,
+             void *cuda_stream);
+
 /* ------------------------------------------------- no-allocation variant - */
 
 /* Bytes of device scratch available to salt_chi2_grad_noalloc: one fixed

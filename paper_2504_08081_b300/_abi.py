@@ -42,8 +42,13 @@ EXPORTS = [
     "salt_bandflux_offsets", "salt_bandflux", "salt_chi2", "salt_chi2_grad", "salt_check",
     "salt_set_option", "salt_get_option", "salt_serve_submit", "salt_serve_poll",
     "salt_serve_cancel", "salt_serve_stats_get", "salt_status_str", "salt_last_error",
-    "salt_chi2_grad_noalloc",
+    "salt_chi2_grad_noalloc", "salt_fit",
 ]
+
+# Fitting (salt_fit): parameter bits, outcome codes.
+SALT_FIT_Z, SALT_FIT_T0, SALT_FIT_X0, SALT_FIT_X1, SALT_FIT_C = 1, 2, 4, 8, 16
+SALT_FIT_DEFAULT_MASK = SALT_FIT_T0 | SALT_FIT_X0 | SALT_FIT_X1 | SALT_FIT_C
+SALT_FIT_MAXITER, SALT_FIT_LINESEARCH, SALT_FIT_INVALID = -1, -2, -3
 
 # Scratch bytes of the no-allocation call (SALT_NOALLOC_SCRATCH_BYTES).
 SALT_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -74,6 +79,11 @@ class BatchDesc(C.Structure):
                 ("fluxerr", C.c_void_p), ("zp", C.c_void_p), ("t0", C.c_void_p),
                 ("z", C.c_void_p), ("x0", C.c_void_p), ("x1", C.c_void_p), ("c", C.c_void_p),
                 ("plan", C.c_void_p), ("validate", C.c_int32)]
+
+
+class FitOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("max_evals", C.c_int32), ("history", C.c_int32),
+                ("free_mask", C.c_int32), ("gtol", C.c_double), ("ftol", C.c_double)]
 
 
 class Request(C.Structure):
@@ -115,6 +125,7 @@ def lib():
     L.salt_chi2.argtypes = [p, C.POINTER(BatchDesc), p, p]
     L.salt_chi2_grad.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
     L.salt_chi2_grad_noalloc.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
+    L.salt_fit.argtypes = [p, C.POINTER(BatchDesc), p, p, C.POINTER(FitOpts), p, p, p, p]
     L.salt_check.argtypes = [p, p]
     L.salt_set_option.argtypes = [p, i32, i64]
     L.salt_get_option.argtypes = [p, i32, C.POINTER(i64)]

@@ -130,6 +130,29 @@ class Salt:
                                                          grad.data_ptr(), _stream(self.device)))
         return chi2, grad
 
+    def fit(self, db: DeviceBatch, lower: torch.Tensor | None = None, upper: torch.Tensor | None = None,
+            free_mask: int = 0, max_iter: int = 0, max_evals: int = 0, history: int = 0,
+            gtol: float = 0.0, ftol: float = 0.0):
+        """Fit every supernova's parameters (one starting sample per supernova in
+        db). lower/upper: float64 [n_sn, 5] device tensors (z, t0, x0, x1, c) or
+        None. Returns theta float64 [n_sn, 5], chi2 float64 [n_sn] and status
+        int32 [n_sn] (device tensors)."""
+        n = db.n_sn
+        for b in (lower, upper):
+            if b is not None and (b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous()
+                                  or b.numel() != 5 * n):
+                raise ValueError("bounds: contiguous float64 [n_sn, 5] CUDA tensors")
+        theta = torch.empty((n, 5), dtype=torch.float64, device=self.device)
+        chi2 = torch.empty(n, dtype=torch.float64, device=self.device)
+        status = torch.empty(n, dtype=torch.int32, device=self.device)
+        opts = _abi.FitOpts(max_iter, max_evals, history, free_mask, gtol, ftol)
+        d = self._desc(db, False)
+        self.ctx.check(_abi.lib().salt_fit(
+            self.ctx.h, C.byref(d), lower.data_ptr() if lower is not None else None,
+            upper.data_ptr() if upper is not None else None, C.byref(opts), theta.data_ptr(),
+            chi2.data_ptr(), status.data_ptr(), _stream(self.device)))
+        return theta, chi2, status
+
     def check(self):
         """Synchronise and raise if a kernel met invalid batch data."""
         self.ctx.check(self.ctx.device_check(_stream(self.device)))

@@ -2,4 +2,5 @@
 the oracle checks and the bench; no photometry arithmetic lives here)."""
 from .synth import (Band, Batch, Model, Request, Workload, add_noise, config1, config2,
                     config3, config4, config5, gaussian_band, make, make_batch, make_model,
-                    subset, template_flux, tophat_band, truth_batch, CONFIG_NAMES, PERTURB)
+                    subset, template_flux, tophat_band, truth_batch, fit_start, CONFIG_NAMES, PERTURB,
+                    FIT_PERTURB)

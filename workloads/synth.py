@@ -263,6 +263,25 @@ def truth_batch(batch: Batch) -> Batch:
                  c=np.asarray(batch.truth["c"], dtype=F32), truth=batch.truth)
 
 
+FIT_PERTURB = dict(t0=2.0, logx0=0.1, x1=0.5, c=0.05)
+
+
+def fit_start(batch: Batch, rng: np.random.Generator, perturb=None) -> Batch:
+    """Starting points for fitting: the same observation table with one sample
+    per SN at the truth, t0, x0, x1 and c perturbed (Gaussian; log-normal for
+    x0) and z kept at the truth (a known redshift). FP32 parameters are
+    rounded to FP32 here, so every consumer reads the same values."""
+    p = FIT_PERTURB if perturb is None else perturb
+    tb = truth_batch(batch)
+    n = tb.n_sn
+    t0 = tb.t0 + rng.normal(0.0, p["t0"], n)
+    x0 = (tb.x0.astype(np.float64) * np.exp(rng.normal(0.0, p["logx0"], n))).astype(F32)
+    x1 = (tb.x1.astype(np.float64) + rng.normal(0.0, p["x1"], n)).astype(F32)
+    c = (tb.c.astype(np.float64) + rng.normal(0.0, p["c"], n)).astype(F32)
+    return Batch(obs_off=tb.obs_off, mjd=tb.mjd, band=tb.band, flux=tb.flux, fluxerr=tb.fluxerr,
+                 zp=tb.zp, par_off=tb.par_off, t0=t0, z=tb.z, x0=x0, x1=x1, c=c, truth=tb.truth)
+
+
 def add_noise(batch: Batch, m_true: np.ndarray, rng: np.random.Generator,
               frac: float = 0.05, noiseless: bool = False) -> None:
     """Observed flux = model flux at the truth + frac-Gaussian noise.
