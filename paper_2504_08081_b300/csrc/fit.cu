@@ -73,7 +73,27 @@ struct State {
 struct Opts {
     double gtol, ftol;
     int max_iter, max_evals, m, mask;
+    // list of the fits still running, rebuilt by every update: the next
+    // evaluation covers only these supernovae (NULL: evaluate all)
+    WorkItem *act;
+    const int64_t *obs_off;
 };
+
+// Count supernova j as running and append its one-sample work item.
+__device__ __forceinline__ void mark_active(const Opts &op, int *n_active, int j) {
+    const int k = atomicAdd(n_active, 1);
+    if (op.act) {
+        WorkItem w;
+        w.obs0 = op.obs_off[j];
+        w.par0 = j;
+        w.bf0 = 0;
+        w.nobs = (int32_t)(op.obs_off[j + 1] - op.obs_off[j]);
+        w.nj = 1;
+        w.jloc0 = 0;
+        w.pad = 0;
+        op.act[k] = w;
+    }
+}
 
 struct Trial {
     double *t0;
@@ -233,7 +253,7 @@ __device__ double cubic_step(double a0, double f0, double g0, double a1, double 
 
 __global__ void k_fit_init(int n, const double *t0, const float *z, const float *x0, const float *x1,
                            const float *c, const double *lower, const double *upper, int mask, State *S,
-                           Trial tr) {
+                           Trial tr, Opts op, int *n_active) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     State st;
@@ -266,6 +286,7 @@ __global__ void k_fit_init(int n, const double *t0, const float *z, const float 
     st.status = ok ? 0 : SALT_FIT_INVALID;
     publish(st, tr, j);
     S[j] = st;
+    if (ok) mark_active(op, n_active, j);
 }
 
 // Take the step to st.xt (chi^2 ft, gradient gt): curvature pair, convergence
@@ -311,7 +332,7 @@ __device__ void accept_step(State &st, const Opts &op, const Trial &tr, int j, d
         st.status = SALT_FIT_MAXITER;
     } else {
         new_direction(st, op, tr, j);
-        atomicAdd(n_active, 1);
+        mark_active(op, n_active, j);
     }
 }
 
@@ -350,7 +371,7 @@ __global__ void k_fit_update(int n, State *S, const double *chi2, const float *g
         }
         st.stage = ST_SEARCH;
         new_direction(st, op, tr, j);
-        atomicAdd(n_active, 1);
+        mark_active(op, n_active, j);
         return;
     }
 
@@ -392,7 +413,7 @@ __global__ void k_fit_update(int n, State *S, const double *chi2, const float *g
 #pragma unroll
                 for (int i = 0; i < NP; ++i) st.xt[i] = st.x[i] + st.alpha * st.d[i] * st.sc[i];
                 publish(st, tr, j);
-                atomicAdd(n_active, 1);
+                mark_active(op, n_active, j);
                 return;
             }
         }
@@ -416,7 +437,7 @@ __global__ void k_fit_update(int n, State *S, const double *chi2, const float *g
                     st.count = 0;
                     st.head = 0;
                     new_direction(st, op, tr, j);
-                    atomicAdd(n_active, 1);
+                    mark_active(op, n_active, j);
                     return;
                 }
                 st.stage = ST_DONE;
@@ -433,7 +454,7 @@ __global__ void k_fit_update(int n, State *S, const double *chi2, const float *g
 #pragma unroll
         for (int i = 0; i < NP; ++i) st.xt[i] = st.x[i] + st.alpha * st.d[i] * st.sc[i];
         publish(st, tr, j);
-        atomicAdd(n_active, 1);
+        mark_active(op, n_active, j);
         return;
     }
     accept_step(st, op, tr, j, ft, gt, n_active);
@@ -468,11 +489,22 @@ int fit_cuda(salt_ctx *ctx, cudaError_t e, const char *what) {
 }  // namespace
 
 // One batched chi^2 + gradient evaluation at the trial points, then the update.
+// One evaluation of the running fits' trial points, then the update (which
+// also lists the fits still running for the next evaluation). With a list
+// (op.act) the warp-unit kernel reads its length on the device, so finished
+// fits cost nothing; without one, the whole batch goes through the plan.
 static int fit_step(salt_ctx *ctx, salt_plan *plan, const BatchDev &b, const OutDev &o, fit::State *S,
-                    const fit::Trial &tr, const fit::Opts &op, int *n_active, int n, cudaStream_t st) {
-    int rc = run_batch(ctx, b, plan, o, MODE_GRAD, st);
-    if (rc != SALT_OK) return rc;
-    cudaError_t e = cudaMemsetAsync(n_active, 0, sizeof(int), st);
+                    const fit::Trial &tr, const fit::Opts &op, int *n_active, int n, int *counter,
+                    void *scratch, cudaStream_t st) {
+    cudaError_t e;
+    if (op.act) {
+        e = launch_unit_items(ctx, 1, op.act, n, counter, scratch, b, o, MODE_GRAD, st, n_active);
+        if (e != cudaSuccess) return fit_cuda(ctx, e, "fit evaluation");
+    } else {
+        const int rc = run_batch(ctx, b, plan, o, MODE_GRAD, st);
+        if (rc != SALT_OK) return rc;
+    }
+    e = cudaMemsetAsync(n_active, 0, sizeof(int), st);
     if (e != cudaSuccess) return fit_cuda(ctx, e, "fit counter");
     fit::k_fit_update<<<(n + 127) / 128, 128, 0, st>>>(n, S, o.chi2, o.grad, tr, op, n_active);
     e = cudaGetLastError();
@@ -524,7 +556,11 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     fit::State *S = nullptr;
     double *t0t = nullptr, *chi2 = nullptr;
     float *zt = nullptr, *x0t = nullptr, *x1t = nullptr, *ct = nullptr, *grad = nullptr;
-    int *n_active = nullptr;
+    int *n_active = nullptr, *counter = nullptr;
+    WorkItem *act = nullptr;  // running fits' work items (warp-unit path)
+    void *uscr = nullptr;     // warp-unit kernel scratch
+    const bool compact = ctx->mp.n_phase <= unit_max_phase() && ctx->mp.bands.n_bands >= 1;
+    const size_t uscr_bytes = compact ? unit_scratch_bytes(n, 1, ctx->mp.bands.n_bands) : 0;
     const size_t fb = (size_t)n * sizeof(float);
     e = cudaMalloc((void **)&S, (size_t)n * sizeof(fit::State));
     if (e == cudaSuccess) e = cudaMalloc((void **)&t0t, (size_t)n * sizeof(double));
@@ -535,10 +571,15 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     if (e == cudaSuccess) e = cudaMalloc((void **)&ct, fb);
     if (e == cudaSuccess) e = cudaMalloc((void **)&grad, 5 * fb);
     if (e == cudaSuccess) e = cudaMalloc((void **)&n_active, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&counter, sizeof(int));
+    if (e == cudaSuccess && compact) e = cudaMalloc((void **)&act, (size_t)n * sizeof(WorkItem));
+    if (e == cudaSuccess && compact) e = cudaMalloc(&uscr, uscr_bytes);
+    if (e == cudaSuccess && compact) e = cudaMemsetAsync(uscr, 0, uscr_bytes, st);  // arrival counters
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_active, 0, sizeof(int), st);
     cudaGraphExec_t exec = nullptr;
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
-        void *ptrs[] = {S, t0t, chi2, zt, x0t, x1t, ct, grad, n_active};
+        void *ptrs[] = {S, t0t, chi2, zt, x0t, x1t, ct, grad, n_active, counter, act, uscr};
         cudaStreamSynchronize(st);
         for (void *q : ptrs)
             if (q) cudaFree(q);
@@ -550,7 +591,7 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
         return rc;
     }
     const fit::Trial tr{t0t, zt, x0t, x1t, ct};
-    const fit::Opts op{o.gtol, o.ftol, o.max_iter, o.max_evals, o.history, o.free_mask};
+    const fit::Opts op{o.gtol, o.ftol, o.max_iter, o.max_evals, o.history, o.free_mask, act, plan.obs_off_d};
     BatchDev b{};
     b.n_sn = n_sn;
     b.n_obs = n_obs;
@@ -562,15 +603,15 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     const OutDev od{nullptr, plan.bf_off_d, chi2, grad, ctx->err_d};
 
     fit::k_fit_init<<<(n + 127) / 128, 128, 0, st>>>(n, bt->t0, bt->z, bt->x0, bt->x1, bt->c, lower, upper,
-                                                      o.free_mask, S, tr);
+                                                      o.free_mask, S, tr, op, n_active);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         rc = fit_cuda(ctx, e, "fit init");
         cleanup();
         return rc;
     }
-    // first evaluation outside capture: it tunes the plan and builds its work list
-    rc = fit_step(ctx, &plan, b, od, S, tr, op, n_active, n, st);
+    // first evaluation outside capture (on the plan path it tunes the kernel choice)
+    rc = fit_step(ctx, &plan, b, od, S, tr, op, n_active, n, counter, uscr, st);
     // then blocks of iterations replayed from one captured graph
     constexpr int BLOCK = 8;
     int evals = 1, active = 1;
@@ -584,7 +625,7 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
         e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
         int rc_cap = SALT_OK;
         for (int k = 0; k < BLOCK && e == cudaSuccess && rc_cap == SALT_OK; ++k)
-            rc_cap = fit_step(ctx, &plan, b, od, S, tr, op, n_active, n, ctx->capture_stream);
+            rc_cap = fit_step(ctx, &plan, b, od, S, tr, op, n_active, n, counter, uscr, ctx->capture_stream);
         const cudaError_t e_end = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e == cudaSuccess) e = e_end;
         if (e == cudaSuccess && rc_cap == SALT_OK) e = cudaGraphInstantiate(&exec, g, 0);
@@ -600,7 +641,7 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
             if (e != cudaSuccess) { rc = fit_cuda(ctx, e, "fit graph"); break; }
         } else {
             for (int k = 0; k < BLOCK && rc == SALT_OK; ++k)
-                rc = fit_step(ctx, &plan, b, od, S, tr, op, n_active, n, st);
+                rc = fit_step(ctx, &plan, b, od, S, tr, op, n_active, n, counter, uscr, st);
             if (rc != SALT_OK) break;
         }
         evals += BLOCK;

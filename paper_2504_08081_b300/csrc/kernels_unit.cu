@@ -73,7 +73,7 @@ __device__ __forceinline__ float warp_sum8_scatter(const float (&v)[8], int lane
 template <int TS, int MODE>
 __global__ void __launch_bounds__(THREADS, 3)
 k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items, int *counter,
-       UnitScratch scr) {
+       UnitScratch scr, const int *n_items_dev) {
     constexpr bool GRAD = MODE == MODE_GRAD;
     constexpr int NE = GRAD ? 3 : 1;  // column responses per sample: E (, E_c, E_z)
     constexpr int ND = 2 * NE;        // row dots per (row, sample): x surfaces M0, M1
@@ -92,7 +92,8 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *D = (float *)wb;                                    wb += al16(4 * (size_t)NPHW * TS * ND);
     int *rowl = (int *)wb;
 
-    const int n_units = n_items * NB;
+    // with n_items_dev the list's length is read on the device (at most n_items)
+    const int n_units = (n_items_dev ? min(*n_items_dev, n_items) : n_items) * NB;
     for (;;) {
         // claim one unit at a time: with few units per warp, claiming ahead
         // would fix the assignment and undo the dynamic balancing
@@ -467,7 +468,8 @@ size_t unit_scratch_bytes(int n_items, int ts, int n_bands) {
 
 template <int TS, int MODE>
 static cudaError_t launch_uk(const salt_ctx *ctx, const WorkItem *items_d, int n_items, int *counter_d,
-                             void *scratch, const BatchDev &b, const OutDev &o, cudaStream_t st) {
+                             void *scratch, const BatchDev &b, const OutDev &o, cudaStream_t st,
+                             const int *n_items_dev) {
     const size_t smem = uk::Lay(TS, MODE == MODE_GRAD).total;
     static std::atomic<int> attr_done[64];
     cudaError_t e;
@@ -491,24 +493,26 @@ static cudaError_t launch_uk(const salt_ctx *ctx, const WorkItem *items_d, int n
     scr.arrive = (int *)((unsigned char *)scratch + (size_t)n_items * TS * nb * uk::NSLOT * sizeof(double));
     e = cudaMemsetAsync(counter_d, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    uk::k_unit<TS, MODE><<<grid, uk::THREADS, smem, st>>>(ctx->mp, b, o, items_d, n_items, counter_d, scr);
+    uk::k_unit<TS, MODE><<<grid, uk::THREADS, smem, st>>>(ctx->mp, b, o, items_d, n_items, counter_d, scr,
+                                                          n_items_dev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unit_items(const salt_ctx *ctx, int ts, const WorkItem *items_d, int n_items, int *counter_d,
-                              void *scratch, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st) {
+                              void *scratch, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st,
+                              const int *n_items_dev) {
     if (n_items <= 0) return cudaSuccess;
     if (ts == 2) {
         switch (mode) {
-            case MODE_BANDFLUX: return launch_uk<2, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
-            case MODE_CHI2: return launch_uk<2, MODE_CHI2>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
-            default: return launch_uk<2, MODE_GRAD>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+            case MODE_BANDFLUX: return launch_uk<2, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, scratch, b, o, st, n_items_dev);
+            case MODE_CHI2: return launch_uk<2, MODE_CHI2>(ctx, items_d, n_items, counter_d, scratch, b, o, st, n_items_dev);
+            default: return launch_uk<2, MODE_GRAD>(ctx, items_d, n_items, counter_d, scratch, b, o, st, n_items_dev);
         }
     }
     switch (mode) {
-        case MODE_BANDFLUX: return launch_uk<1, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
-        case MODE_CHI2: return launch_uk<1, MODE_CHI2>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
-        default: return launch_uk<1, MODE_GRAD>(ctx, items_d, n_items, counter_d, scratch, b, o, st);
+        case MODE_BANDFLUX: return launch_uk<1, MODE_BANDFLUX>(ctx, items_d, n_items, counter_d, scratch, b, o, st, n_items_dev);
+        case MODE_CHI2: return launch_uk<1, MODE_CHI2>(ctx, items_d, n_items, counter_d, scratch, b, o, st, n_items_dev);
+        default: return launch_uk<1, MODE_GRAD>(ctx, items_d, n_items, counter_d, scratch, b, o, st, n_items_dev);
     }
 }
 

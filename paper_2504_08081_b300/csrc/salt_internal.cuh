@@ -158,8 +158,11 @@ cudaError_t launch_bandwarp_items(const salt_ctx *ctx, int ts, const WorkItem *i
                                   cudaStream_t st);
 int bandwarp_item_samples();
 int bandwarp_max_phase();
+// n_items_dev (optional): device int read by the kernel as the list's length
+// (clamped to n_items, which sizes the grid and the scratch).
 cudaError_t launch_unit_items(const salt_ctx *ctx, int ts, const WorkItem *items_d, int n_items, int *counter_d,
-                              void *scratch, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st);
+                              void *scratch, const BatchDev &b, const OutDev &o, int mode, cudaStream_t st,
+                              const int *n_items_dev = nullptr);
 int unit_max_phase();
 size_t unit_scratch_bytes(int n_items, int ts, int n_bands);
 cudaError_t launch_validate(const salt_ctx *ctx, const BatchDev &b, int *flag, cudaStream_t st);
