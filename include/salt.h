@@ -102,6 +102,32 @@ int salt_init_model(const salt_model_desc *model, const salt_band_desc *bands, i
 /* Stop the serving engine (pending requests are cancelled), free everything. */
 void salt_destroy(salt_ctx *ctx);
 
+/* Register one more bandpass on a live context (the paper's
+ * register_bandpass, Implementation, paragraph on bandpasses.py). Same rules
+ * and weights as a band passed to salt_init_model; *band_id = its id (the
+ * previous band count). Not concurrently with other calls on the context;
+ * waits for device work that may read the old band tables. Plans made before
+ * drop their work lists, scratch, tuned choices and captured graphs on their
+ * next use (which then must not be inside a stream capture).
+ * SALT_ERR_INVALID for a bad band or a full registry (SALT_MAX_BANDS). */
+int salt_register_band(salt_ctx *ctx, const salt_band_desc *band, int32_t *band_id);
+
+/* Read a bandpass from a text file (the paper's load_bandpass_from_file).
+ * One sample per line: wavelength and transmission separated by blanks, tabs
+ * or a comma (further columns ignored); '#' starts a comment; blank lines are
+ * skipped. Wavelengths are multiplied by wave_scale (1 for Angstrom, 10 for
+ * nm) and must be finite, positive and strictly ascending; at least 2 samples.
+ * step > 0 resamples the curve, taken as piecewise linear between its samples,
+ * at the multiples of step inside [first, last wavelength]; step = 0 keeps
+ * the file's samples. Host only (no device work).
+ *   wave, trans: HOST float64 [capacity] out; *n: the number of samples.
+ *   wave = trans = NULL with capacity = 0 only sets *n (size query).
+ *   ctx: optional, receives the error text for salt_last_error.
+ * SALT_ERR_INVALID for an unreadable or malformed file, bad arguments, or a
+ * capacity below *n. */
+int salt_band_load(salt_ctx *ctx, const char *path, double wave_scale, double step, double *wave,
+                   double *trans, int32_t capacity, int32_t *n);
+
 /* ---------------------------------------------------------------- batches - */
 
 /* A ragged batch (the paper's vmap over data instances, Implementation,

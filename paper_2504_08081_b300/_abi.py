@@ -42,7 +42,7 @@ EXPORTS = [
     "salt_bandflux_offsets", "salt_bandflux", "salt_chi2", "salt_chi2_grad", "salt_check",
     "salt_set_option", "salt_get_option", "salt_serve_submit", "salt_serve_poll",
     "salt_serve_cancel", "salt_serve_stats_get", "salt_status_str", "salt_last_error",
-    "salt_chi2_grad_noalloc", "salt_fit",
+    "salt_chi2_grad_noalloc", "salt_fit", "salt_register_band", "salt_band_load",
 ]
 
 # Fitting (salt_fit): parameter bits, outcome codes.
@@ -126,6 +126,8 @@ def lib():
     L.salt_chi2_grad.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
     L.salt_chi2_grad_noalloc.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
     L.salt_fit.argtypes = [p, C.POINTER(BatchDesc), p, p, C.POINTER(FitOpts), p, p, p, p]
+    L.salt_register_band.argtypes = [p, C.POINTER(BandDesc), C.POINTER(i32)]
+    L.salt_band_load.argtypes = [p, C.c_char_p, C.c_double, C.c_double, p, p, i32, C.POINTER(i32)]
     L.salt_check.argtypes = [p, p]
     L.salt_set_option.argtypes = [p, i32, i64]
     L.salt_get_option.argtypes = [p, i32, C.POINTER(i64)]
@@ -249,3 +251,19 @@ def batch_desc(obs_off, par_off, dev: dict, plan: Plan | None = None, validate: 
                      _ptr(dev["t0"]), _ptr(dev["z"]), _ptr(dev["x0"]), _ptr(dev["x1"]),
                      _ptr(dev["c"]), plan.h.value if plan is not None else None,
                      1 if validate else 0)
+
+
+def load_band(path: str, step: float = 5.0, wave_scale: float = 1.0):
+    """salt_band_load: (wave, trans) float64 arrays from a bandpass text file,
+    resampled at multiples of `step` Angstrom (0 keeps the file's samples)."""
+    n = C.c_int32()
+    rc = lib().salt_band_load(None, str(path).encode(), wave_scale, step, None, None, 0, C.byref(n))
+    if rc != SALT_OK:
+        raise SaltError(rc, f"cannot load bandpass {path}")
+    wave = np.empty(n.value)
+    trans = np.empty(n.value)
+    rc = lib().salt_band_load(None, str(path).encode(), wave_scale, step, wave.ctypes.data,
+                              trans.ctypes.data, n.value, C.byref(n))
+    if rc != SALT_OK:
+        raise SaltError(rc, f"cannot load bandpass {path}")
+    return wave, trans

@@ -60,6 +60,33 @@ bool finite_all(const float *v, size_t n) {
     return true;
 }
 
+// Check one band and append its samples and trapezoid weights
+// lambda T Delta / (h c Z_b) (FP64, rounded to float32) to lam / w.
+bool band_tables(const salt_band_desc &bd, std::vector<float> &lam, std::vector<float> &w) {
+    if (bd.n < 2 || !bd.wave || !bd.trans) return false;
+    for (int k = 0; k < bd.n; ++k) {
+        if (!std::isfinite(bd.wave[k]) || !std::isfinite(bd.trans[k]) || !(bd.wave[k] > 0)) return false;
+        if (k > 0 && !(bd.wave[k] > bd.wave[k - 1])) return false;
+    }
+    const double hc = kPlanck * kLightAA;
+    const int K = bd.n;
+    std::vector<double> wk(K);
+    double Z = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double lo = (k > 0) ? bd.wave[k - 1] : bd.wave[k];
+        const double hi = (k + 1 < K) ? bd.wave[k + 1] : bd.wave[k];
+        const double delta = 0.5 * (hi - lo);
+        wk[k] = bd.wave[k] * bd.trans[k] * delta / hc;
+        Z += wk[k] * kAB * kLightAA / (bd.wave[k] * bd.wave[k]);
+    }
+    if (!(Z > 0) || !std::isfinite(Z)) return false;
+    for (int k = 0; k < K; ++k) {
+        lam.push_back((float)bd.wave[k]);
+        w.push_back((float)(wk[k] / Z));
+    }
+    return true;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ model
@@ -78,14 +105,6 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     if (!finite_all(md->m0, ng) || !finite_all(md->m1, ng)) return SALT_ERR_INVALID;
     for (int q = 0; q < 4; ++q)
         if (!std::isfinite(md->cl[q])) return SALT_ERR_INVALID;
-    for (int b = 0; b < n_bands; ++b) {
-        const salt_band_desc &bd = bands[b];
-        if (bd.n < 2 || !bd.wave || !bd.trans) return SALT_ERR_INVALID;
-        for (int k = 0; k < bd.n; ++k) {
-            if (!std::isfinite(bd.wave[k]) || !std::isfinite(bd.trans[k]) || !(bd.wave[k] > 0)) return SALT_ERR_INVALID;
-            if (k > 0 && !(bd.wave[k] > bd.wave[k - 1])) return SALT_ERR_INVALID;
-        }
-    }
     ctx = new (std::nothrow) salt_ctx();
     if (!ctx) return SALT_ERR_OOM;
     ctx->device = device;
@@ -127,29 +146,14 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     std::vector<float> lam_h, w_h;
     mp.bands.n_bands = n_bands;
     int off = 0;
-    const double hc = kPlanck * kLightAA;
     for (int b = 0; b < n_bands; ++b) {
         const salt_band_desc &bd = bands[b];
-        const int K = bd.n;
-        std::vector<double> wk(K);
-        double Z = 0.0;
-        for (int k = 0; k < K; ++k) {
-            const double lo = (k > 0) ? bd.wave[k - 1] : bd.wave[k];
-            const double hi = (k + 1 < K) ? bd.wave[k + 1] : bd.wave[k];
-            const double delta = 0.5 * (hi - lo);
-            wk[k] = bd.wave[k] * bd.trans[k] * delta / hc;
-            Z += wk[k] * kAB * kLightAA / (bd.wave[k] * bd.wave[k]);
-        }
-        if (!(Z > 0) || !std::isfinite(Z)) { delete ctx; return SALT_ERR_INVALID; }
+        if (!band_tables(bd, lam_h, w_h)) { delete ctx; return SALT_ERR_INVALID; }
         mp.bands.off[b] = off;
-        mp.bands.n[b] = K;
+        mp.bands.n[b] = bd.n;
         mp.bands.lam_lo[b] = (float)bd.wave[0];
-        mp.bands.lam_hi[b] = (float)bd.wave[K - 1];
-        for (int k = 0; k < K; ++k) {
-            lam_h.push_back((float)bd.wave[k]);
-            w_h.push_back((float)(wk[k] / Z));
-        }
-        off += K;
+        mp.bands.lam_hi[b] = (float)bd.wave[bd.n - 1];
+        off += bd.n;
     }
     mp.bands.k_total = off;
     // interleaved (M0, M1) rows with an even pitch so every row starts on 16 bytes
@@ -185,6 +189,8 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     mp.g01 = ctx->g01_d;
     mp.band_lam = ctx->band_lam_d;
     mp.band_w = ctx->band_w_d;
+    ctx->host_lam = std::move(lam_h);
+    ctx->host_w = std::move(w_h);
     ctx->serve_mem = serve_mem_bytes;
     if (serve_mem_bytes > 0) {
         ctx->serve = serve_create(ctx, serve_mem_bytes);
@@ -213,6 +219,47 @@ extern "C" void salt_destroy(salt_ctx *ctx) {
     (void)cudaGetLastError();
 }
 
+extern "C" int salt_register_band(salt_ctx *ctx, const salt_band_desc *band, int32_t *band_id) {
+    if (!ctx || !band || !band_id) return SALT_ERR_INVALID;
+    if (ctx->mp.bands.n_bands >= SALT_MAX_BANDS)
+        return set_err(ctx, SALT_ERR_INVALID, "band registry full (SALT_MAX_BANDS)");
+    std::vector<float> lam = ctx->host_lam, w = ctx->host_w;
+    if (!band_tables(*band, lam, w))
+        return set_err(ctx, SALT_ERR_INVALID, "band needs >= 2 finite samples, ascending positive wavelengths "
+                                              "and a positive AB integral");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    float *lam_d = nullptr, *w_d = nullptr;
+    cudaError_t e = cudaMalloc(&lam_d, lam.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&w_d, w.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(lam_d, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w_d, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (lam_d) cudaFree(lam_d);
+        if (w_d) cudaFree(w_d);
+        return cuda_err(ctx, e, "register band");
+    }
+    // cudaFree waits for work in flight that may still read the old tables
+    cudaFree(ctx->band_lam_d);
+    cudaFree(ctx->band_w_d);
+    ctx->band_lam_d = lam_d;
+    ctx->band_w_d = w_d;
+    BandTable &bt = ctx->mp.bands;
+    const int b = bt.n_bands;
+    bt.off[b] = bt.k_total;
+    bt.n[b] = band->n;
+    bt.lam_lo[b] = (float)band->wave[0];
+    bt.lam_hi[b] = (float)band->wave[band->n - 1];
+    bt.k_total += band->n;
+    bt.n_bands = b + 1;
+    ctx->mp.band_lam = lam_d;
+    ctx->mp.band_w = w_d;
+    ctx->host_lam = std::move(lam);
+    ctx->host_w = std::move(w);
+    ++ctx->band_gen;  // plans drop their work lists, scratch and graphs on next use
+    *band_id = b;
+    return SALT_OK;
+}
+
 // ------------------------------------------------------------------ planning
 
 namespace salt {
@@ -236,6 +283,7 @@ int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_
     }
     p->ctx = ctx;
     p->device = ctx->device;
+    p->band_gen = ctx->band_gen;
     p->n_sn = n_sn;
     p->n_obs = obs_off[n_sn];
     p->n_par = par_off[n_sn];
@@ -493,9 +541,31 @@ static bool replay_graph(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b
     return true;
 }
 
+// Drop a plan's work lists (and their scratch), captured graphs and tuned
+// choices; the offsets stay. Used when the context's bands changed.
+static void plan_reset_work(salt_plan *p) {
+    for (auto &kv : p->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    p->graphs.clear();
+    for (auto &kv : p->lists) {
+        if (kv.second.d) cudaFree(kv.second.d);
+        if (kv.second.scratch) cudaFree(kv.second.scratch);
+    }
+    p->lists.clear();
+    for (int &c : p->choice) c = -1;
+}
+
 int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const OutDev &o, int mode,
               cudaStream_t st) {
     salt_plan *p = const_cast<salt_plan *>(cplan);  // tuning state and work lists are a cache
+    if (p->band_gen != ctx->band_gen) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs != cudaStreamCaptureStatusNone)
+            return set_err(ctx, SALT_ERR_INVALID, "bands changed: run the plan once outside stream capture");
+        if (!p->temporary) plan_reset_work(p);
+        p->band_gen = ctx->band_gen;
+    }
     if (ctx->kernel == SALT_KERNEL_DIRECT) {
         ctx->last_kernel = SALT_KERNEL_DIRECT * 16;
         cudaError_t e = launch_direct(ctx, b, o, mode, st);

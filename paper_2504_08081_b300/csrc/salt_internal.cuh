@@ -105,6 +105,7 @@ struct salt_plan {
     };
     std::map<int, ItemList> lists;
     int choice[3] = {-1, -1, -1};  // tuned configuration key per mode (-1 = not tuned yet)
+    int band_gen = 0;               // the context's band generation the work state was built for
     int *counter_d = nullptr;      // dynamic work counter of the persistent kernels
     bool temporary = false;
     // Captured CUDA graphs, one per (mode, launch configuration): the batch and
@@ -139,6 +140,8 @@ struct salt_ctx {
     int last_kernel = 0;   // SALT_KERNEL_* x 16 + tile of the last batch launch (0 = none yet)
     cudaStream_t capture_stream = nullptr;  // private stream for graph capture (created on first use)
     std::vector<double> host_cl;  // colour-law coefficients (for serving validation)
+    std::vector<float> host_lam, host_w;  // band tables as uploaded (for registering bands)
+    int band_gen = 0;             // bumped by every band registration
     salt::ServeEngine *serve = nullptr;
     size_t serve_mem = 0;
     std::mutex mu;  // guards last_error for serve_* callers

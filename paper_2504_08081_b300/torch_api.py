@@ -163,6 +163,17 @@ class Salt:
     def set_tile(self, tile: int):
         self.ctx.set_option(_abi.SALT_OPT_TILE_SAMPLES, tile)
 
+    def register_band(self, wave, trans) -> int:
+        """Add a bandpass (wavelength [A], transmission) to this context; returns its id."""
+        w = np.ascontiguousarray(wave, np.float64)
+        t = np.ascontiguousarray(trans, np.float64)
+        if w.shape != t.shape or w.ndim != 1:
+            raise ValueError("wave and trans: 1-D arrays of one length")
+        bd = _abi.BandDesc(len(w), w.ctypes.data, t.ctypes.data)
+        bid = C.c_int32()
+        self.ctx.check(_abi.lib().salt_register_band(self.ctx.h, C.byref(bd), C.byref(bid)))
+        return bid.value
+
     def set_graphs(self, on: bool):
         self.ctx.set_option(_abi.SALT_OPT_GRAPHS, 1 if on else 0)
 
