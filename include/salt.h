@@ -64,14 +64,22 @@ typedef struct salt_plan salt_plan;
 
 /* ---------------------------------------------------------------- model --- */
 
-/* Model grid (Eq. 1 surfaces) on uniform axes. HOST pointers, copied.
+/* Model grid (Eq. 1 surfaces). HOST pointers, copied.
  *   phase axis: phase0 + r*dphase, r < n_phase (days); wave axis: wave0 +
  *   j*dwave, j < n_wave (Angstrom). n_phase, n_wave >= 4.
  *   m0, m1: row-major [n_phase][n_wave] float32.
  *   cl: n_cl == 4 colour-law coefficients a1..a4 of
  *       P(x) = (1 - sum a) x + a1 x^2 + a2 x^3 + a3 x^4 + a4 x^5,
  *       x = (lambda - 4302.57)/(5428.55 - 4302.57), CL = -P on [cl_lo, cl_hi],
- *       linear continuation outside. */
+ *       linear continuation outside.
+ *   phase_nodes [n_phase], wave_nodes [n_wave]: optional non-uniform axes
+ *       (SALT3-NIR-style grids; the paper's "dedicated interpolation
+ *       routines", Implementation, last but one paragraph): strictly
+ *       ascending finite node positions; when given, phase0/dphase (or
+ *       wave0/dwave) are ignored. A coordinate is located by binary search
+ *       and the Keys weights apply to its fraction of the local interval
+ *       (index space); derivatives carry 1/(local interval width). NULL =
+ *       the uniform axis. */
 typedef struct {
     int32_t n_phase, n_wave;
     double phase0, dphase, wave0, dwave;
@@ -79,6 +87,7 @@ typedef struct {
     int32_t n_cl;
     const double *cl;
     double cl_lo, cl_hi;
+    const double *phase_nodes, *wave_nodes;
 } salt_model_desc;
 
 /* A bandpass (paper: Bandpass / register_bandpass): n >= 2 samples of

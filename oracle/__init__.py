@@ -24,7 +24,8 @@ class _Model(C.Structure):
                 ("phase0", C.c_double), ("dphase", C.c_double),
                 ("wave0", C.c_double), ("dwave", C.c_double),
                 ("m0", C.POINTER(C.c_double)), ("m1", C.POINTER(C.c_double)),
-                ("cl", C.c_double * 4), ("cl_lo", C.c_double), ("cl_hi", C.c_double)]
+                ("cl", C.c_double * 4), ("cl_lo", C.c_double), ("cl_hi", C.c_double),
+                ("pnode", C.POINTER(C.c_double)), ("wnode", C.POINTER(C.c_double))]
 
 
 class _Band(C.Structure):
@@ -47,6 +48,8 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(build())
         d, i32, i64, p = C.c_double, C.c_int32, C.c_int64, C.c_void_p
+        _lib.om_axis_taps_nodes.restype = C.c_int
+        _lib.om_axis_taps_nodes.argtypes = [d, p, i32, C.POINTER(i32), p, p]
         _lib.om_axis_taps.restype = C.c_int
         _lib.om_axis_taps.argtypes = [d, d, d, i32, C.POINTER(i32), p, p]
         _lib.om_surface.restype = d
@@ -83,9 +86,15 @@ class Oracle:
         self.m0 = np.ascontiguousarray(model.m0, dtype=np.float64)
         self.m1 = np.ascontiguousarray(model.m1, dtype=np.float64)
         cl = (C.c_double * 4)(*[float(v) for v in model.cl])
+        nodes = []
+        for name in ("phase_nodes", "wave_nodes"):
+            v = getattr(model, name, None)
+            v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+            self._keep.append(v)
+            nodes.append(None if v is None else _dp(v))
         self.model = _Model(model.n_phase, model.n_wave, model.phase0, model.dphase,
                             model.wave0, model.dwave, _dp(self.m0), _dp(self.m1), cl,
-                            model.cl_lo, model.cl_hi)
+                            model.cl_lo, model.cl_hi, nodes[0], nodes[1])
         nb = len(bands)
         self.bands = (_Band * max(nb, 1))()
         for b, band in enumerate(bands):

@@ -60,6 +60,9 @@ typedef struct {
     const double *m0, *m1; /* row-major [n_phase][n_wave] */
     double cl[4];
     double cl_lo, cl_hi;
+    /* non-uniform axes: ascending node positions [n_phase] / [n_wave]; NULL =
+     * the uniform axis phase0 + r dphase / wave0 + j dwave */
+    const double *pnode, *wnode;
 } om_model;
 
 typedef struct {
@@ -116,6 +119,38 @@ int om_axis_taps(double x, double x0, double dx, int32_t n, int32_t *first,
     return 4;
 }
 
+/* The same on an axis with ascending, possibly non-uniform nodes (the SALT3 /
+ * SALT3-NIR "dedicated interpolation routines", Implementation, last but one
+ * paragraph; reading: the interval i is found by search, the coordinate is
+ * mapped to index space u = i + (x - x_i)/(x_{i+1} - x_i), and the Keys kernel
+ * applies in u, so a uniform axis gives exactly the taps above). */
+int om_axis_taps_nodes(double x, const double *node, int32_t n, int32_t *first,
+                       double w[4], double dw[4])
+{
+    if (n < 2 || !(x >= node[0] && x <= node[n - 1])) return 0;
+    int32_t lo = 0, hi = n - 1; /* node[lo] <= x, and x <= node[hi] */
+    while (hi - lo > 1) {
+        int32_t mid = (lo + hi) / 2;
+        if (node[mid] <= x) lo = mid; else hi = mid;
+    }
+    int32_t i = lo;
+    double h = node[i + 1] - node[i];
+    double t = (x - node[i]) / h;
+    if (i == 0 || i == n - 2) {
+        *first = i;
+        w[0] = 1.0 - t;  dw[0] = -1.0 / h;
+        w[1] = t;        dw[1] = 1.0 / h;
+        return 2;
+    }
+    *first = i - 1;
+    for (int m = 0; m < 4; ++m) {
+        double s = t + 1.0 - (double)m; /* signed index-space distance to node i-1+m */
+        w[m] = keys_kernel(s);
+        dw[m] = keys_kernel_deriv(s) / h;
+    }
+    return 4;
+}
+
 /* Surface value at (phase p, rest wavelength lam), with d/dp and d/dlam.
  * Zero (with zero derivatives) outside the grid. */
 double om_surface(const om_model *m, const double *G, double p, double lam,
@@ -123,8 +158,10 @@ double om_surface(const om_model *m, const double *G, double p, double lam,
 {
     int32_t fp = 0, fl = 0;
     double wp[4], dwp[4], wl[4], dwl[4];
-    int np = om_axis_taps(p, m->phase0, m->dphase, m->n_phase, &fp, wp, dwp);
-    int nl = om_axis_taps(lam, m->wave0, m->dwave, m->n_wave, &fl, wl, dwl);
+    int np = m->pnode ? om_axis_taps_nodes(p, m->pnode, m->n_phase, &fp, wp, dwp)
+                      : om_axis_taps(p, m->phase0, m->dphase, m->n_phase, &fp, wp, dwp);
+    int nl = m->wnode ? om_axis_taps_nodes(lam, m->wnode, m->n_wave, &fl, wl, dwl)
+                      : om_axis_taps(lam, m->wave0, m->dwave, m->n_wave, &fl, wl, dwl);
     double v = 0.0, vp = 0.0, vl = 0.0;
     for (int a = 0; a < np; ++a)
         for (int b = 0; b < nl; ++b) {

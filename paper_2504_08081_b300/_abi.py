@@ -66,7 +66,8 @@ class ModelDesc(C.Structure):
                 ("wave0", C.c_double), ("dwave", C.c_double),
                 ("m0", C.c_void_p), ("m1", C.c_void_p),
                 ("n_cl", C.c_int32), ("cl", C.c_void_p),
-                ("cl_lo", C.c_double), ("cl_hi", C.c_double)]
+                ("cl_lo", C.c_double), ("cl_hi", C.c_double),
+                ("phase_nodes", C.c_void_p), ("wave_nodes", C.c_void_p)]
 
 
 class BandDesc(C.Structure):
@@ -165,10 +166,12 @@ class Context:
         m0 = np.ascontiguousarray(model.m0, dtype=np.float32)
         m1 = np.ascontiguousarray(model.m1, dtype=np.float32)
         cl = np.ascontiguousarray(model.cl, dtype=np.float64)
+        nodes = [getattr(model, k, None) for k in ("phase_nodes", "wave_nodes")]
+        nodes = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in nodes]
         md = ModelDesc(model.n_phase, model.n_wave, model.phase0, model.dphase, model.wave0,
                        model.dwave, m0.ctypes.data, m1.ctypes.data, len(cl), cl.ctypes.data,
-                       model.cl_lo, model.cl_hi)
-        keep = []
+                       model.cl_lo, model.cl_hi, *[None if v is None else v.ctypes.data for v in nodes])
+        keep = [v for v in nodes if v is not None]
         arr = (BandDesc * max(1, len(bands)))()
         for b, band in enumerate(bands):
             w = np.ascontiguousarray(band.wave, dtype=np.float64)

@@ -97,9 +97,17 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     *out = nullptr;
     salt_ctx *ctx = nullptr;
     if (!md || (!bands && n_bands > 0) || n_bands < 0 || n_bands > SALT_MAX_BANDS) return SALT_ERR_INVALID;
-    if (md->n_phase < 4 || md->n_wave < 4 || md->n_phase > 256 || !(md->dphase > 0) || !(md->dwave > 0) ||
-        !std::isfinite(md->phase0) || !std::isfinite(md->wave0) || !md->m0 || !md->m1 || md->n_cl != 4 ||
-        !md->cl || !(md->cl_lo < md->cl_hi))
+    auto axis_ok = [](const double *nodes, int n, double x0, double dx) {
+        if (!nodes) return dx > 0 && std::isfinite(x0) && std::isfinite(dx);
+        for (int i = 0; i < n; ++i) {
+            if (!std::isfinite(nodes[i])) return false;
+            if (i > 0 && !(nodes[i] > nodes[i - 1])) return false;
+        }
+        return true;
+    };
+    if (md->n_phase < 4 || md->n_wave < 4 || md->n_phase > 256 || !md->m0 || !md->m1 || md->n_cl != 4 ||
+        !md->cl || !(md->cl_lo < md->cl_hi) || !axis_ok(md->phase_nodes, md->n_phase, md->phase0, md->dphase) ||
+        !axis_ok(md->wave_nodes, md->n_wave, md->wave0, md->dwave))
         return SALT_ERR_INVALID;
     const size_t ng = (size_t)md->n_phase * md->n_wave;
     if (!finite_all(md->m0, ng) || !finite_all(md->m1, ng)) return SALT_ERR_INVALID;
@@ -118,13 +126,19 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     ModelParams &mp = ctx->mp;
     mp.n_phase = md->n_phase;
     mp.n_wave = md->n_wave;
-    mp.phase0 = (float)md->phase0;
-    mp.inv_dphase = (float)(1.0 / md->dphase);
-    mp.phase_max = (float)(md->phase0 + (md->n_phase - 1) * md->dphase);
-    mp.wave0 = (float)md->wave0;
-    mp.inv_dwave = (float)(1.0 / md->dwave);
-    mp.wave_max = (float)(md->wave0 + (md->n_wave - 1) * md->dwave);
-    mp.dwave = (float)md->dwave;
+    // axis ends (and, on uniform axes, the inverse step); non-uniform axes keep
+    // their nodes and inverse interval widths on the device
+    const double p0 = md->phase_nodes ? md->phase_nodes[0] : md->phase0;
+    const double p1 = md->phase_nodes ? md->phase_nodes[md->n_phase - 1] : md->phase0 + (md->n_phase - 1) * md->dphase;
+    const double w0 = md->wave_nodes ? md->wave_nodes[0] : md->wave0;
+    const double w1 = md->wave_nodes ? md->wave_nodes[md->n_wave - 1] : md->wave0 + (md->n_wave - 1) * md->dwave;
+    mp.phase0 = (float)p0;
+    mp.inv_dphase = (float)(md->phase_nodes ? (md->n_phase - 1) / (p1 - p0) : 1.0 / md->dphase);
+    mp.phase_max = (float)p1;
+    mp.wave0 = (float)w0;
+    mp.inv_dwave = (float)(md->wave_nodes ? (md->n_wave - 1) / (w1 - w0) : 1.0 / md->dwave);
+    mp.wave_max = (float)w1;
+    mp.dwave = (float)(md->wave_nodes ? (w1 - w0) / (md->n_wave - 1) : md->dwave);
     const double a[4] = {md->cl[0], md->cl[1], md->cl[2], md->cl[3]};
     mp.cl_p[0] = (float)(1.0 - a[0] - a[1] - a[2] - a[3]);
     for (int q = 0; q < 4; ++q) mp.cl_p[q + 1] = (float)a[q];
@@ -184,6 +198,24 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
         if ((e = cudaMemcpy(ctx->band_w_d, w_h.data(), w_h.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
             return fail(e, "upload bands");
     }
+    if (md->phase_nodes || md->wave_nodes) {
+        // [phase nodes | phase inverse widths | wave nodes | wave inverse widths], each n long
+        const int np = md->n_phase, nw = md->n_wave;
+        std::vector<float> nodes(2 * (size_t)np + 2 * (size_t)nw, 0.f);
+        auto fill = [&](const double *x, int n, float *node, float *inv) {
+            for (int i = 0; i < n; ++i) node[i] = (float)x[i];
+            for (int i = 0; i + 1 < n; ++i) inv[i] = (float)(1.0 / (x[i + 1] - x[i]));
+        };
+        if (md->phase_nodes) fill(md->phase_nodes, np, nodes.data(), nodes.data() + np);
+        if (md->wave_nodes) fill(md->wave_nodes, nw, nodes.data() + 2 * np, nodes.data() + 2 * np + nw);
+        if ((e = cudaMalloc(&ctx->nodes_d, nodes.size() * sizeof(float))) != cudaSuccess)
+            return fail(e, "cudaMalloc nodes");
+        if ((e = cudaMemcpy(ctx->nodes_d, nodes.data(), nodes.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return fail(e, "upload nodes");
+        if (md->phase_nodes) { mp.pnode = ctx->nodes_d; mp.pinv = ctx->nodes_d + np; }
+        if (md->wave_nodes) { mp.wnode = ctx->nodes_d + 2 * np; mp.winv = ctx->nodes_d + 2 * np + nw; }
+    }
     if ((e = cudaMalloc(&ctx->err_d, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
     if ((e = cudaMemset(ctx->err_d, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "memset err");
     mp.g01 = ctx->g01_d;
@@ -213,6 +245,7 @@ extern "C" void salt_destroy(salt_ctx *ctx) {
     if (ctx->band_lam_d) cudaFree(ctx->band_lam_d);
     if (ctx->band_w_d) cudaFree(ctx->band_w_d);
     if (ctx->err_d) cudaFree(ctx->err_d);
+    if (ctx->nodes_d) cudaFree(ctx->nodes_d);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
     cudaSetDevice(prev);

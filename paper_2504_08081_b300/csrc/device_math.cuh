@@ -47,6 +47,29 @@ __device__ __forceinline__ bool axis_locate(float x, float x0, float inv_dx, flo
     return true;
 }
 
+// Interval i, fraction t and the interval's inverse width iw (for the
+// derivatives) of x on a model axis: the uniform axis when node is NULL (the
+// arithmetic of axis_locate), else by binary search over the ascending node
+// positions, t being the fraction of the local interval (the index-space
+// reading of the Keys kernel on a non-uniform axis). False outside the axis.
+__device__ __forceinline__ bool axis_find(float x, float x0, float inv_dx, float xmax, int n, const float *node,
+                                          const float *inv, int &i, float &t, float &iw) {
+    if (!node) {
+        iw = inv_dx;
+        return axis_locate(x, x0, inv_dx, xmax, n, i, t);
+    }
+    if (!(x >= x0 && x <= xmax)) return false;
+    int lo = 0, hi = n - 1;  // node[lo] <= x <= node[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(node + mid) <= x) lo = mid; else hi = mid;
+    }
+    i = lo;
+    iw = __ldg(inv + lo);
+    t = fminf((x - __ldg(node + lo)) * iw, 1.0f);
+    return true;
+}
+
 // Weights (and optionally derivatives w.r.t. x) for a located interval.
 // Written with selects only (no runtime index into the tap arrays), so the
 // taps stay in registers.
@@ -84,6 +107,40 @@ __device__ __forceinline__ void axis_taps(float x, float x0, float inv_dx, float
         return;
     }
     axis_taps_from<DERIV>(i, t, n, inv_dx, tp);
+}
+
+// The model's two axes.
+__device__ __forceinline__ bool phase_find(const ModelParams &m, float p, int &i, float &t, float &iw) {
+    return axis_find(p, m.phase0, m.inv_dphase, m.phase_max, m.n_phase, m.pnode, m.pinv, i, t, iw);
+}
+__device__ __forceinline__ bool wave_find(const ModelParams &m, float lam, int &i, float &t, float &iw) {
+    return axis_find(lam, m.wave0, m.inv_dwave, m.wave_max, m.n_wave, m.wnode, m.winv, i, t, iw);
+}
+
+// Taps on a model axis (all weights zero outside it).
+template <bool DERIV>
+__device__ __forceinline__ void phase_taps(const ModelParams &m, float p, Taps4 &tp) {
+    int i;
+    float t, iw;
+    if (!phase_find(m, p, i, t, iw)) {
+        tp.first = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { tp.w[q] = 0.f; if (DERIV) tp.dw[q] = 0.f; }
+        return;
+    }
+    axis_taps_from<DERIV>(i, t, m.n_phase, iw, tp);
+}
+template <bool DERIV>
+__device__ __forceinline__ void wave_taps(const ModelParams &m, float lam, Taps4 &tp) {
+    int i;
+    float t, iw;
+    if (!wave_find(m, lam, i, t, iw)) {
+        tp.first = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { tp.w[q] = 0.f; if (DERIV) tp.dw[q] = 0.f; }
+        return;
+    }
+    axis_taps_from<DERIV>(i, t, m.n_wave, iw, tp);
 }
 
 // SALT2-form colour law CL(lambda) and dCL/dlambda (linear outside [cl_lo, cl_hi]).

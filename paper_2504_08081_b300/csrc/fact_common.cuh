@@ -38,9 +38,10 @@ __device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, c
             const float lr = lam[k] * a;
             int iv;
             float t;
-            axis_locate(lr, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+            float iw;
+            wave_find(m, lr, iv, t, iw);
             Taps4 tl;
-            axis_taps_from<false>(iv, t, NW, m.inv_dwave, tl);
+            axis_taps_from<false>(iv, t, NW, iw, tl);
             float dcl;
             const float cl = colour_law(m, lr, dcl);
             const float A = wk[k] * exp2f(kColour * c * cl);
@@ -91,9 +92,10 @@ __device__ __forceinline__ void ebuild3(const ModelParams &m, const float *lam, 
             const float lr = lam[k] * a;
             int iv;
             float t;
-            axis_locate(lr, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+            float iw;
+            wave_find(m, lr, iv, t, iw);
             Taps4 tl;
-            axis_taps_from<true>(iv, t, NW, m.inv_dwave, tl);
+            axis_taps_from<true>(iv, t, NW, iw, tl);
             float dcl;
             const float cl = colour_law(m, lr, dcl);
             const float A = wk[k] * exp2f(kColour * c * cl);
@@ -153,9 +155,10 @@ __device__ __forceinline__ void eadjoint(const ModelParams &m, const float *lam,
         const float lr = lam[k] * a;
         int iv;
         float t;
-        axis_locate(lr, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+        float iw;
+            wave_find(m, lr, iv, t, iw);
         Taps4 tl;
-        axis_taps_from<true>(iv, t, NW, m.inv_dwave, tl);
+        axis_taps_from<true>(iv, t, NW, iw, tl);
         float dcl;
         const float cl = colour_law(m, lr, dcl);
         const float A = wk[k] * exp2f(kColour * c * cl);

@@ -229,9 +229,9 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                         }
                         if (kf[s] <= kl[s]) {
                             int iv; float t;
-                            axis_locate(lam[kf[s]] * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            { float iw_; wave_find(m, lam[kf[s]] * a, iv, t, iw_); }
                             clo = min(clo, fk::first_tap(iv, NW));
-                            axis_locate(lam[kl[s]] * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            { float iw_; wave_find(m, lam[kl[s]] * a, iv, t, iw_); }
                             chi = max(chi, fk::first_tap(iv, NW) + 3);
                         }
                     }
@@ -247,8 +247,8 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                         for (int s = 0; s < TS; ++s) {
                             if (s >= ns || sPj[PJ_OK * NJ_MAX + j0 + s] == 0.f) continue;
                             const float p = (float)(mj - sT0[j0 + s]) * sPj[PJ_A * NJ_MAX + j0 + s];
-                            int iv; float t;
-                            if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
+                            int iv; float t, iwp;
+                            if (phase_find(m, p, iv, t, iwp)) {
                                 const int first = fk::first_tap(iv, NP);
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) msk[(first + q) >> 5] |= 1u << ((first + q) & 31);
@@ -365,9 +365,9 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                             const float a = sPj[PJ_A * NJ_MAX + j], x0 = sPj[PJ_X0 * NJ_MAX + j];
                             const float x1 = sPj[PJ_X1 * NJ_MAX + j];
                             const float p = (float)(mj - sT0[j]) * a;
-                            int iv; float t;
-                            if (okj && axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
-                                axis_taps_from<GRAD>(iv, t, NP, m.inv_dphase, tp);
+                            int iv; float t, iwp;
+                            if (okj && phase_find(m, p, iv, t, iwp)) {
+                                axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                                 for (int mm = 0; mm < 4; ++mm) {
                                     const float2 dv = *reinterpret_cast<const float2 *>(D + ((tp.first + mm) * TS + s) * 2);

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_direct(ModelParams m, BatchDev b, OutDe
         }
         const float p = (float)(b.mjd[i] - t0) * a;
         Taps4 tp;
-        axis_taps<GRAD>(p, m.phase0, m.inv_dphase, m.phase_max, m.n_phase, tp);
+        phase_taps<GRAD>(m, p, tp);
         float accB = 0.f, acc1 = 0.f, accC = 0.f, accP = 0.f, accL = 0.f;
         const int off = m.bands.off[bnd], K = m.bands.n[bnd];
         for (int k = lane; k < K; k += 32) {
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_direct(ModelParams m, BatchDev b, OutDe
             const float wk = __ldg(m.band_w + off + k);
             const float lr = lam * a;
             Taps4 tl;
-            axis_taps<GRAD>(lr, m.wave0, m.inv_dwave, m.wave_max, m.n_wave, tl);
+            wave_taps<GRAD>(m, lr, tl);
             float dcl;
             const float cl = colour_law(m, lr, dcl);
             const float C = exp2f(kColour * c * cl);

@@ -326,9 +326,9 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         sPj[PJ_KL * TJ + j] = __int_as_float(kl);
                         if (kf <= kl) {
                             int iv; float t;
-                            axis_locate(lam[kf] * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            { float iw_; wave_find(m, lam[kf] * a, iv, t, iw_); }
                             atomicMin(&sMisc[4], first_tap(iv, NW));
-                            axis_locate(lam[kl] * a, m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                            { float iw_; wave_find(m, lam[kl] * a, iv, t, iw_); }
                             atomicMax(&sMisc[5], first_tap(iv, NW) + 3);
                         }
                     }
@@ -342,8 +342,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             if (sPj[PJ_OK * TJ + j] != 0.f) {
                                 const int i = ordb[il];
                                 const float p = (float)(sMjd[i] - sT0[j]) * sPj[PJ_A * TJ + j];
-                                int iv; float t;
-                                if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t))
+                                int iv; float t, iwp;
+                                if (phase_find(m, p, iv, t, iwp))
                                     first = first_tap(iv, NP);
                             }
                         }
@@ -460,9 +460,9 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 if (act) {
                                     const int i = ordb[il];
                                     const float p = (float)(sMjd[i] - t0) * a;
-                                    int iv; float t;
-                                    if (okj && axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
-                                        axis_taps_from<GRAD>(iv, t, NP, m.inv_dphase, tp);
+                                    int iv; float t, iwp;
+                                    if (okj && phase_find(m, p, iv, t, iwp)) {
+                                        axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                                         for (int mm = 0; mm < 4; ++mm) {
                                             const float2 dv = *reinterpret_cast<const float2 *>(sD + ((tp.first + mm) * TJ + j) * 2);

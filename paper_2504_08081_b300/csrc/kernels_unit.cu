@@ -153,9 +153,9 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             }
             if (kf[s] <= kl[s]) {
                 int iv; float t;
-                axis_locate(lam[kf[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                { float iw_; wave_find(m, lam[kf[s]] * pa[s], iv, t, iw_); }
                 clo = min(clo, fk::first_tap(iv, NW));
-                axis_locate(lam[kl[s]] * pa[s], m.wave0, m.inv_dwave, m.wave_max, NW, iv, t);
+                { float iw_; wave_find(m, lam[kl[s]] * pa[s], iv, t, iw_); }
                 chi = max(chi, fk::first_tap(iv, NW) + 3);
             }
         }
@@ -245,8 +245,8 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     for (int s = 0; s < TS; ++s) {
                         if (!pok[s]) continue;
                         const float p = (float)(oMjd[il] - pt0[s]) * pa[s];
-                        int iv; float t;
-                        if (axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
+                        int iv; float t, iwp;
+                        if (phase_find(m, p, iv, t, iwp)) {
                             const int first = fk::first_tap(iv, NP);
                             const int w0 = first >> 5, sh = first & 31;
                             const unsigned lo = 0xfu << sh;                       // rows in word w0
@@ -365,9 +365,9 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     if (act && s < ns) {
                         const float a = pa[s];
                         const float p = (float)(mj - pt0[s]) * a;
-                        int iv; float t;
-                        if (pok[s] && axis_locate(p, m.phase0, m.inv_dphase, m.phase_max, NP, iv, t)) {
-                            axis_taps_from<GRAD>(iv, t, NP, m.inv_dphase, tp);
+                        int iv; float t, iwp;
+                        if (pok[s] && phase_find(m, p, iv, t, iwp)) {
+                            axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                             for (int mm = 0; mm < 4; ++mm) {
                                 const float *dv = D + ((tp.first + mm) * TS + s) * ND;

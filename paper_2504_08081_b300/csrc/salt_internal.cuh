@@ -44,6 +44,11 @@ struct ModelParams {
     const float2 *__restrict__ g01;      // [n_phase][nw_pitch] interleaved (M0, M1)
     const float *__restrict__ band_lam;  // flat band wavelengths (observer frame)
     const float *__restrict__ band_w;    // flat weights lambda T Delta / (h c Z_b)
+    // non-uniform axes (NULL = uniform): node positions and 1/(node[i+1] - node[i])
+    const float *__restrict__ pnode;
+    const float *__restrict__ pinv;
+    const float *__restrict__ wnode;
+    const float *__restrict__ winv;
     BandTable bands;
 };
 
@@ -131,6 +136,7 @@ struct salt_ctx {
     salt::ModelParams mp{};
     float2 *g01_d = nullptr;
     float *band_lam_d = nullptr, *band_w_d = nullptr;
+    float *nodes_d = nullptr;  // non-uniform axes: phase nodes, inverse widths, wave nodes, inverse widths
     int *err_d = nullptr;
     std::string last_error;
     int kernel = SALT_KERNEL_AUTO;

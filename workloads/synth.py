@@ -49,13 +49,20 @@ class Model:
     cl: np.ndarray  # float64 [4]
     cl_lo: float = CL_RANGE[0]
     cl_hi: float = CL_RANGE[1]
+    # non-uniform axes: ascending node positions (None = uniform axis)
+    phase_nodes: np.ndarray | None = None
+    wave_nodes: np.ndarray | None = None
 
     @property
     def phase_max(self) -> float:
+        if self.phase_nodes is not None:
+            return float(self.phase_nodes[-1])
         return self.phase0 + (self.n_phase - 1) * self.dphase
 
     @property
     def wave_max(self) -> float:
+        if self.wave_nodes is not None:
+            return float(self.wave_nodes[-1])
         return self.wave0 + (self.n_wave - 1) * self.dwave
 
 
@@ -136,6 +143,42 @@ def make_model(rng: np.random.Generator, wave_max: float = 9200.0,
     cl = rng.uniform(-0.5, 0.5, size=4)
     return Model(phase0=p0, dphase=dp, n_phase=n_phase, wave0=wave0, dwave=dwave,
                  n_wave=n_wave, m0=m0.astype(F32), m1=m1.astype(F32), cl=cl)
+
+
+def make_model_nodes(rng: np.random.Generator, phase_nodes, wave_nodes, cl_amp: float = 0.5) -> Model:
+    """Synthetic surfaces on non-uniform axes (same recipe as make_model, the
+    smooth factors taken at the node positions, the edge taper over 3 nodes).
+    Colour-law coefficients ~ U(-cl_amp, cl_amp): grids reaching the NIR need
+    small ones, since the law continues linearly with its slope at cl_hi."""
+    p = np.asarray(phase_nodes, dtype=np.float64)
+    w = np.asarray(wave_nodes, dtype=np.float64)
+    n_phase, n_wave = len(p), len(w)
+    u = ((p - p[0]) / (p[-1] - p[0]))[:, None]
+    v = ((w - w[0]) / (w[-1] - w[0]))[None, :]
+    env = (_taper(n_phase) * np.exp(-p * p / (2 * 15.0 ** 2)))[:, None] * _taper(n_wave)[None, :]
+
+    def sines(amp_bound):
+        s = np.zeros((n_phase, n_wave))
+        for _ in range(3):
+            a = rng.uniform(-amp_bound, amp_bound)
+            f, g = rng.integers(1, 4, size=2)
+            b, c = rng.uniform(0, 2 * np.pi, size=2)
+            s += a * np.sin(2 * np.pi * f * u + b) * np.sin(2 * np.pi * g * v + c)
+        return s
+
+    m0 = 0.1 * env * (1.0 + 0.3 * sines(1.0))
+    m1 = 0.01 * env * sines(1.0)
+    cl = rng.uniform(-cl_amp, cl_amp, size=4)
+    return Model(phase0=float(p[0]), dphase=float(p[1] - p[0]), n_phase=n_phase, wave0=float(w[0]),
+                 dwave=float(w[1] - w[0]), n_wave=n_wave, m0=m0.astype(F32), m1=m1.astype(F32), cl=cl,
+                 phase_nodes=p, wave_nodes=w)
+
+
+# SALT3-NIR-shaped axes: phase denser around peak; wavelength 10 A to 9200 A,
+# then 40 A steps out to 20000 A.
+NIR_PHASE_NODES = np.concatenate([np.arange(-20.0, -5.0, 1.0), np.arange(-5.0, 5.0, 0.5),
+                                  np.arange(5.0, 50.01, 1.5)])
+NIR_WAVE_NODES = np.concatenate([np.arange(2000.0, 9200.0, 10.0), np.arange(9200.0, 20000.01, 40.0)])
 
 
 # ----------------------------------------------------------------------------
@@ -443,6 +486,21 @@ def config4(seed: int = 1004, n_req: int = 20000, rate_per_s: float = 1000.0) ->
     reqs = [Request(arrival_s=float(t[i]), want_grad=bool(grad[i]), batch=subset(big, [i]))
             for i in range(n_req)]
     return Workload(CONFIG_NAMES[4], model, bands, big, requests=reqs)
+
+
+def config_nir(seed: int = 1006, n_sn: int = 200, n_samples: int = 4) -> Workload:
+    """Non-uniform SALT3-NIR-shaped grid (66 x 991 nodes), 3 optical + 3 NIR
+    Gaussian bands (centres 4500-16500 A, 5 A sampling), obs ~ U{20..120},
+    z ~ U(0.01, 0.2), n_samples draws around the truth per SN; colour-law
+    coefficients ~ U(-0.02, 0.02)."""
+    rng = np.random.default_rng(seed)
+    model = make_model_nodes(rng, NIR_PHASE_NODES, NIR_WAVE_NODES, cl_amp=0.02)
+    bands = _six_bands(rng, np.array([4500.0, 6000.0, 7500.0, 10200.0, 12500.0, 16500.0]))
+    n_obs = rng.integers(20, 121, size=n_sn)
+    z = rng.uniform(0.01, 0.2, size=n_sn)
+    b = make_batch(rng, model, bands, n_obs, z, np.full(n_sn, n_samples, dtype=np.int64),
+                   perturb=PERTURB)
+    return Workload("nir_nonuniform_200sn", model, bands, b)
 
 
 def make(config: int, **kw) -> Workload:
