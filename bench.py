@@ -310,6 +310,61 @@ def secondary(args, salt_mod, torch, dev, stream):
     from paper_2504_08081_b300 import serving as SV
     out[W.CONFIG_NAMES[4]] = SV.run_serving_bench(dev.index or 0)
     out["fit_" + W.CONFIG_NAMES[2]] = fit_secondary(dev, args.cpu_seconds)
+    out["nested_" + W.CONFIG_NAMES[3]] = nested_secondary(dev, args.cpu_seconds)
+    return out
+
+
+def nested_secondary(dev, cpu_seconds, n_live=1024, n_batch=256, n_steps=10):
+    """Nested sampling (salt_nested) of the 256-supernova differentiation
+    batch with 1024 live points each (its 1024 samples per supernova as live
+    points): observed fluxes are this library's bandfluxes at the truth plus
+    5 % noise, prior box t0 +- 5 d, x0 x [0.5, 1.5], x1 in [-3, 3], c in
+    [-0.3, 0.3]; beside it, the reference sampler on the FP64 oracle for one
+    supernova with the same settings."""
+    import torch
+    import oracle
+    import oracle.nested as NS
+    from paper_2504_08081_b300.torch_api import Salt
+    wl = make_workload(3, 0)
+    s = Salt(wl.model, wl.bands, device=dev.index or 0)
+    tb = W.truth_batch(wl.batch)
+    m_true = s.bandflux(s.upload(tb, plan=False)).cpu().numpy()
+    W.add_noise(tb, m_true, np.random.default_rng(2026))
+    n = tb.n_sn
+    ref = np.stack([tb.z, tb.t0, tb.x0, tb.x1, tb.c], axis=1).astype(np.float64)
+    lo, hi = ref.copy(), ref.copy()
+    lo[:, 1], hi[:, 1] = ref[:, 1] - 5.0, ref[:, 1] + 5.0
+    lo[:, 2], hi[:, 2] = 0.5 * ref[:, 2], 1.5 * ref[:, 2]
+    lo[:, 3], hi[:, 3] = -3.0, 3.0
+    lo[:, 4], hi[:, 4] = -0.3, 0.3
+    db = s.upload(tb)
+    T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev).contiguous()  # noqa: E731
+    kw = dict(n_live=n_live, n_batch=n_batch, n_steps=n_steps, seed=1)
+    s.nested(db, T(lo), T(hi), **kw)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    logz, err, mean, std, st = s.nested(db, T(lo), T(hi), **kw)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = st.cpu().numpy()
+    iters = int(st.max())
+    evals = n * (n_live + iters * n_batch * n_steps)
+    out = {"supernovae": n, "n_live": n_live, "n_batch": n_batch, "n_steps": n_steps,
+           "wall_s": wall, "iterations_max": iters, "likelihood_evals": evals,
+           "likelihood_evals_per_s": evals / wall, "posteriors_per_s": n / wall,
+           "logz_err_median": float(np.median(err.cpu().numpy())),
+           "timing": "wall clock around salt_nested (it synchronises)"}
+    s.close()
+    o = oracle.Oracle(wl.model, wl.bands)
+    t0 = time.perf_counter()
+    r = NS.run_one(o, tb, 0, lo[0], hi[0], n_live=n_live, n_batch=n_batch, n_steps=n_steps, seed=1,
+                   max_iter=max(1, int(cpu_seconds)))
+    t_cpu = time.perf_counter() - t0
+    ev_cpu = n_live + r["iterations"] * n_batch * n_steps
+    out["cpu_baseline"] = {"value": ev_cpu / t_cpu, "unit": "likelihood evals/s", "cores": o.threads,
+                           "kind": "oracle",
+                           "sample": f"supernova 0, {r['iterations']} iterations of the reference sampler "
+                                     f"(FP64 oracle chi^2, OpenMP over proposals, {t_cpu:.1f} s)"}
     return out
 
 

@@ -324,6 +324,47 @@ int salt_fit(salt_ctx *ctx, const salt_batch *batch, const double *lower, const 
              const salt_fit_opts *opts, double *theta, double *chi2, int32_t *status,
              void *cuda_stream);
 
+/* ------------------------------------------------------- nested sampling - */
+
+/* Options of salt_nested; zero fields take the defaults. */
+typedef struct {
+    int32_t n_live;     /* live points per supernova (default 256; 2..1024) */
+    int32_t n_batch;    /* live points replaced per iteration (default n_live / 4; < n_live) */
+    int32_t n_steps;    /* random-walk steps per replacement (default 20) */
+    int32_t max_iter;   /* iterations (default 2000) */
+    int32_t free_mask;  /* SALT_FIT_* bits of the sampled parameters (default t0, x0, x1, c) */
+    int32_t reserved;   /* 0 */
+    uint64_t seed;      /* Philox4x32-10 key */
+    double dlogz;       /* stop when the live points could add < dlogz to log Z (default 0.1) */
+} salt_nested_opts;
+
+/* Nested sampling of every supernova's posterior and evidence (the paper's
+ * nested-sampling example, Implementation, first paragraph), all supernovae
+ * in lockstep on the device. Likelihood L = exp(-chi^2/2) (the library's
+ * chi^2), prior uniform in the box [lower, upper] of the sampled parameters.
+ * Per iteration the n_batch lowest live points are removed (the j-th removal
+ * with N - j points live shrinks log X by 1/(N - j)) and replaced by the end
+ * points of n_batch random-walk chains (n_steps steps each, started at
+ * survivors picked uniformly; step = f * survivors' standard deviation *
+ * standard normal; accepted inside the box above the last removed log L;
+ * f *= exp(acceptance - 1/2) per iteration, clipped to [1e-3, 10]). Random
+ * numbers: Philox4x32-10 with the seed as key (Salmon et al., SC'11), so a
+ * seed reproduces a run; every chi^2 evaluation uses the CTA-factorised
+ * kernel at a fixed tile.
+ *   batch: one sample per supernova (par_off[s] = s) holding the values of
+ *     the parameters that are not sampled (z, usually); validate ignored.
+ *   lower, upper: DEVICE float64 [n_sn][5] prior box (finite for sampled
+ *     parameters).
+ *   logz, logz_err (sqrt(H / n_live)): DEVICE float64 [n_sn] out; mean, std:
+ *     DEVICE float64 [n_sn][5] out (posterior moments); status: DEVICE int32
+ *     [n_sn] out (iterations used, SALT_FIT_MAXITER, or SALT_FIT_INVALID for
+ *     an empty or non-finite box).
+ * Synchronises cuda_stream; allocates its scratch (about 60 x n_live bytes
+ * per supernova plus the chains) for the call. */
+int salt_nested(salt_ctx *ctx, const salt_batch *batch, const double *lower, const double *upper,
+                const salt_nested_opts *opts, double *logz, double *logz_err, double *mean, double *std,
+                int32_t *status, void *cuda_stream);
+
 /* ------------------------------------------------- no-allocation variant - */
 
 /* Bytes of device scratch available to salt_chi2_grad_noalloc: one fixed

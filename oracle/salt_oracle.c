@@ -349,28 +349,34 @@ void om_bandflux_batch(const om_model *m, const om_band *bands, const om_batch *
     }
 }
 
-/* chi2[j] for every sample j; grad (nullable) is [n_par][5] = d chi2 / d(z, t0, x0, x1, c). */
+/* chi2[j] for every sample j; grad (nullable) is [n_par][5] = d chi2 / d(z, t0, x0, x1, c).
+ * Samples are independent: the threads share them out one sample at a time. */
 void om_chi2_batch(const om_model *m, const om_band *bands, const om_batch *bt, double *chi2,
                    double *grad)
 {
+    int64_t n_par = bt->n_sn > 0 ? bt->par_off[bt->n_sn] : 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(om_threads)
-    for (int64_t s = 0; s < bt->n_sn; ++s) {
-        int64_t o0 = bt->obs_off[s], o1 = bt->obs_off[s + 1];
-        for (int64_t j = bt->par_off[s]; j < bt->par_off[s + 1]; ++j) {
-            double par[5] = {bt->z[j], bt->t0[j], bt->x0[j], bt->x1[j], bt->c[j]};
-            double x2 = 0.0, g[5] = {0, 0, 0, 0, 0};
-            for (int64_t o = o0; o < o1; ++o) {
-                double dB[5];
-                double B = om_bandflux_one(m, &bands[bt->band[o]], bt->mjd[o], bt->zp[o], par,
-                                           grad ? dB : NULL);
-                double r = (bt->flux[o] - B) / bt->fluxerr[o];
-                x2 += r * r;
-                if (grad)
-                    for (int q = 0; q < 5; ++q) g[q] += -2.0 * r / bt->fluxerr[o] * dB[q];
-            }
-            chi2[j] = x2;
-            if (grad)
-                for (int q = 0; q < 5; ++q) grad[5 * j + q] = g[q];
+    for (int64_t j = 0; j < n_par; ++j) {
+        int64_t lo = 0, hi = bt->n_sn; /* supernova s of sample j: par_off[s] <= j < par_off[s+1] */
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) / 2;
+            if (bt->par_off[mid] <= j) lo = mid; else hi = mid;
         }
+        int64_t s = lo;
+        int64_t o0 = bt->obs_off[s], o1 = bt->obs_off[s + 1];
+        double par[5] = {bt->z[j], bt->t0[j], bt->x0[j], bt->x1[j], bt->c[j]};
+        double x2 = 0.0, g[5] = {0, 0, 0, 0, 0};
+        for (int64_t o = o0; o < o1; ++o) {
+            double dB[5];
+            double B = om_bandflux_one(m, &bands[bt->band[o]], bt->mjd[o], bt->zp[o], par,
+                                       grad ? dB : NULL);
+            double r = (bt->flux[o] - B) / bt->fluxerr[o];
+            x2 += r * r;
+            if (grad)
+                for (int q = 0; q < 5; ++q) g[q] += -2.0 * r / bt->fluxerr[o] * dB[q];
+        }
+        chi2[j] = x2;
+        if (grad)
+            for (int q = 0; q < 5; ++q) grad[5 * j + q] = g[q];
     }
 }

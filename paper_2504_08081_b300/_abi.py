@@ -42,7 +42,7 @@ EXPORTS = [
     "salt_bandflux_offsets", "salt_bandflux", "salt_chi2", "salt_chi2_grad", "salt_check",
     "salt_set_option", "salt_get_option", "salt_serve_submit", "salt_serve_poll",
     "salt_serve_cancel", "salt_serve_stats_get", "salt_status_str", "salt_last_error",
-    "salt_chi2_grad_noalloc", "salt_fit", "salt_register_band", "salt_band_load",
+    "salt_chi2_grad_noalloc", "salt_fit", "salt_register_band", "salt_band_load", "salt_nested",
 ]
 
 # Fitting (salt_fit): parameter bits, outcome codes.
@@ -87,6 +87,12 @@ class FitOpts(C.Structure):
                 ("free_mask", C.c_int32), ("gtol", C.c_double), ("ftol", C.c_double)]
 
 
+class NestedOpts(C.Structure):
+    _fields_ = [("n_live", C.c_int32), ("n_batch", C.c_int32), ("n_steps", C.c_int32),
+                ("max_iter", C.c_int32), ("free_mask", C.c_int32), ("reserved", C.c_int32),
+                ("seed", C.c_uint64), ("dlogz", C.c_double)]
+
+
 class Request(C.Structure):
     _fields_ = [("n_obs", C.c_int32), ("n_par", C.c_int32), ("want_grad", C.c_int32),
                 ("mjd", C.c_void_p), ("band", C.c_void_p), ("flux", C.c_void_p),
@@ -127,6 +133,7 @@ def lib():
     L.salt_chi2_grad.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
     L.salt_chi2_grad_noalloc.argtypes = [p, C.POINTER(BatchDesc), p, p, p]
     L.salt_fit.argtypes = [p, C.POINTER(BatchDesc), p, p, C.POINTER(FitOpts), p, p, p, p]
+    L.salt_nested.argtypes = [p, C.POINTER(BatchDesc), p, p, C.POINTER(NestedOpts), p, p, p, p, p, p]
     L.salt_register_band.argtypes = [p, C.POINTER(BandDesc), C.POINTER(i32)]
     L.salt_band_load.argtypes = [p, C.c_char_p, C.c_double, C.c_double, p, p, i32, C.POINTER(i32)]
     L.salt_check.argtypes = [p, p]

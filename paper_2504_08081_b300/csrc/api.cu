@@ -659,6 +659,22 @@ int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const Ou
     return SALT_OK;
 }
 
+// Launch a plan with a fixed configuration (no autotuning, no graph replay):
+// for callers whose results must not depend on timing (the same kernel family
+// and tile give bitwise the same results run to run).
+int run_batch_fixed(salt_ctx *ctx, const BatchDev &b, salt_plan *p, const OutDev &o, int mode, cudaStream_t st,
+                    int family, int tile) {
+    if (p->band_gen != ctx->band_gen) {
+        plan_reset_work(p);
+        p->band_gen = ctx->band_gen;
+    }
+    const int key = cfg_key(family, tile);
+    int rc = build_items(ctx, p, key, st);
+    if (rc != SALT_OK) return rc;
+    cudaError_t e = launch_key(ctx, p, key, b, o, mode, st);
+    return e == cudaSuccess ? SALT_OK : cuda_err(ctx, e, "kernel launch");
+}
+
 }  // namespace salt
 
 extern "C" int salt_plan_create(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_t *par_off,

@@ -192,5 +192,8 @@ int plan_build(salt_ctx *ctx, int64_t n_sn, const int64_t *obs_off, const int64_
 void plan_free(salt_plan *p, cudaStream_t st);
 int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *plan, const OutDev &o, int mode,
               cudaStream_t st);
+// The plan with one fixed configuration (no autotuning, no graph replay).
+int run_batch_fixed(salt_ctx *ctx, const BatchDev &b, salt_plan *p, const OutDev &o, int mode, cudaStream_t st,
+                    int family, int tile);
 
 }  // namespace salt

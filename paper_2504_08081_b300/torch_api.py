@@ -153,6 +153,28 @@ class Salt:
             chi2.data_ptr(), status.data_ptr(), _stream(self.device)))
         return theta, chi2, status
 
+    def nested(self, db: DeviceBatch, lower: torch.Tensor, upper: torch.Tensor, free_mask: int = 0,
+               n_live: int = 0, n_batch: int = 0, n_steps: int = 0, max_iter: int = 0, seed: int = 1,
+               dlogz: float = 0.0):
+        """Nested sampling per supernova (one sample per supernova in db holds
+        the values of the parameters not sampled). lower/upper: float64
+        [n_sn, 5] device tensors, the uniform prior box. Returns logz, logz_err
+        (float64 [n_sn]), mean, std (float64 [n_sn, 5]), status (int32 [n_sn])."""
+        n = db.n_sn
+        for b in (lower, upper):
+            if b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous() or b.numel() != 5 * n:
+                raise ValueError("prior box: contiguous float64 [n_sn, 5] CUDA tensors")
+        f64 = dict(dtype=torch.float64, device=self.device)
+        logz, err = torch.empty(n, **f64), torch.empty(n, **f64)
+        mean, std = torch.empty((n, 5), **f64), torch.empty((n, 5), **f64)
+        status = torch.empty(n, dtype=torch.int32, device=self.device)
+        opts = _abi.NestedOpts(n_live, n_batch, n_steps, max_iter, free_mask, 0, seed, dlogz)
+        d = self._desc(db, False)
+        self.ctx.check(_abi.lib().salt_nested(
+            self.ctx.h, C.byref(d), lower.data_ptr(), upper.data_ptr(), C.byref(opts), logz.data_ptr(),
+            err.data_ptr(), mean.data_ptr(), std.data_ptr(), status.data_ptr(), _stream(self.device)))
+        return logz, err, mean, std, status
+
     def check(self):
         """Synchronise and raise if a kernel met invalid batch data."""
         self.ctx.check(self.ctx.device_check(_stream(self.device)))
