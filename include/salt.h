@@ -209,12 +209,13 @@ int salt_check(salt_ctx *ctx, void *cuda_stream);
 
 typedef enum {
     SALT_OPT_KERNEL = 1,       /* SALT_KERNEL_* : which kernel family batch calls use */
-    SALT_OPT_TILE_SAMPLES = 2, /* samples per tile for the forced kernel families (0 = default) */
+    SALT_OPT_TILE_SAMPLES = 2, /* samples per tile for the forced kernel families: 1, 2, 4, 8, 16
+                                  (CTA family; the warp families take 1 or 2) or 0 = default */
     SALT_OPT_GRAPHS = 3,       /* 1 (default) = a plan call repeated with the same batch and output
                                   pointers, mode and kernel is captured into a CUDA graph once and
                                   replayed on later such calls; 0 = always launch directly */
     SALT_OPT_SERVE_CHUNK = 4,  /* serving: samples per chunk (default 64) */
-    SALT_OPT_LAST_KERNEL = 5   /* read-only: SALT_KERNEL_* x 16 + samples per tile of the kernel
+    SALT_OPT_LAST_KERNEL = 5   /* read-only: SALT_KERNEL_* x 32 + samples per tile of the kernel
                                   the last batch call on this context launched (0 = none yet) */
 } salt_option;
 

@@ -485,7 +485,7 @@ static int tune(salt_ctx *ctx, salt_plan *p, const BatchDev &b, const OutDev &o,
                 int *best_key) {
     std::vector<int> cands;
     const double mean = p->n_sn > 0 ? (double)p->n_par / (double)p->n_sn : 1.0;
-    for (int t : {1, 2, 4, 8})
+    for (int t : {1, 2, 4, 8})  // 16-sample tiles measured slower than 8 on every workload
         if (t == 1 || mean >= 0.75 * t) cands.push_back(cfg_key(FAM_CTA, t));
     if (ctx->mp.n_phase <= bandwarp_max_phase()) {
         cands.push_back(cfg_key(FAM_WARP, 1));
@@ -600,7 +600,7 @@ int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const Ou
         p->band_gen = ctx->band_gen;
     }
     if (ctx->kernel == SALT_KERNEL_DIRECT) {
-        ctx->last_kernel = SALT_KERNEL_DIRECT * 16;
+        ctx->last_kernel = SALT_KERNEL_DIRECT * 32;
         cudaError_t e = launch_direct(ctx, b, o, mode, st);
         return e == cudaSuccess ? SALT_OK : cuda_err(ctx, e, "kernel launch");
     }
@@ -649,7 +649,7 @@ int run_batch(salt_ctx *ctx, const BatchDev &b, const salt_plan *cplan, const Ou
     if (rc != SALT_OK) return rc;
     const int fam = cfg_family(key);
     ctx->last_kernel = (fam == FAM_UNIT ? SALT_KERNEL_UNIT : fam == FAM_WARP ? SALT_KERNEL_BANDWARP
-                                                                             : SALT_KERNEL_FACTORISED) * 16 +
+                                                                             : SALT_KERNEL_FACTORISED) * 32 +
                        cfg_tile(key);
     cudaError_t e;
     if (ctx->use_graphs && !p->temporary && replay_graph(ctx, p, key, b, o, mode, st, &e))
@@ -821,7 +821,8 @@ extern "C" int salt_set_option(salt_ctx *ctx, int32_t option, int64_t value) {
             ctx->kernel = (int)value;
             return SALT_OK;
         case SALT_OPT_TILE_SAMPLES:
-            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) return SALT_ERR_INVALID;
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+                return SALT_ERR_INVALID;
             ctx->tile_samples = (int)value;
             return SALT_OK;
         case SALT_OPT_GRAPHS:

@@ -40,7 +40,9 @@ constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memo
 struct Lay {
     size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, t0, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, total;
     __host__ __device__ Lay(int tj, bool grad, int n_phase) {
-        const int wps = WARPS / tj;
+        const int wps = tj >= WARPS ? 1 : WARPS / tj;
+        const int nslot = tj > WARPS ? tj : WARPS;  // (warp, sample) slots
+        const bool stage = tj <= 8;                 // 16-sample tiles read band samples through L1
         size_t o = 0;
         ord = o;     o = al16(o + 4 * OBS_MAX);
         zpf = o;     o = al16(o + 4 * OBS_MAX);
@@ -49,8 +51,8 @@ struct Lay {
         flux = o;    o = al16(o + 4 * OBS_MAX);
         sig = o;     o = al16(o + 4 * OBS_MAX);
         bst = o;     o = al16(o + 4 * (2 * SALT_MAX_BANDS + 2));
-        lam = o;     o = al16(o + 4 * KTOT);
-        wk = o;      o = al16(o + 4 * KTOT);
+        lam = o;     o = al16(o + (stage ? 4 * KTOT : 0));
+        wk = o;      o = al16(o + (stage ? 4 * KTOT : 0));
         pj = o;      o = al16(o + 4 * 8 * tj);
         t0 = o;      o = al16(o + 8 * tj);
         rowmask = o; o = al16(o + 4 * (NPH_MAX / 32));
@@ -60,9 +62,9 @@ struct Lay {
         Ep = o;      o = al16(o + (wps > 1 ? 4 * (size_t)WARPS * WMAX : 0));
         Q = o;       o = al16(o + (grad ? 4 * (size_t)THREADS * tj : 0));
         D = o;       o = al16(o + 4 * (size_t)n_phase * tj * 2);
-        Yw = o;      o = al16(o + (grad ? 4 * (size_t)WARPS * n_phase : 0));
-        kst = o;     o = al16(o + (size_t)WARPS * 8 * 32);
-        red = o;     o = al16(o + 8 * (size_t)WARPS * 8);
+        Yw = o;      o = al16(o + (grad ? 4 * (size_t)nslot * n_phase : 0));
+        kst = o;     o = al16(o + 4 * (size_t)WARPS * 64);
+        red = o;     o = al16(o + 8 * (size_t)nslot * 8);
         total = o;
     }
 };
@@ -142,7 +144,9 @@ __global__ void __launch_bounds__(THREADS, 3)
 k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items,
        int *counter) {
     constexpr bool GRAD = MODE == MODE_GRAD;
-    constexpr int WPS = WARPS / TJ;  // warps per sample
+    constexpr int WPS = TJ >= WARPS ? 1 : WARPS / TJ;  // warps per sample
+    constexpr int SPW = TJ > WARPS ? TJ / WARPS : 1;   // samples per warp
+    // (warp, jj) -> sample (warp / WPS) * SPW + jj, slot warp * SPW + jj
     extern __shared__ __align__(16) unsigned char smem[];
     const Lay L(TJ, GRAD, m.n_phase);
     int *sOrd = (int *)(smem + L.ord);
@@ -159,7 +163,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *sEp = (float *)(smem + L.Ep);   // [WARPS][WMAX] per-warp partials (WPS > 1)
     float *sQ = (float *)(smem + L.Q);     // [THREADS][TJ] reverse-GEMM partials, then Q[col][j]
     float *sD = (float *)(smem + L.D);     // [n_phase][TJ][2]
-    float *sYw = (float *)(smem + L.Yw);   // [WARPS][n_phase] adjoint rows per warp
+    float *sYw = (float *)(smem + L.Yw);   // [slots][n_phase] adjoint rows per (warp, sample)
     double *sMjd = (double *)(smem + L.mjd);
     int *sBand = (int *)(smem + L.band);
     float *sFlux = (float *)(smem + L.flux);
@@ -173,7 +177,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     // per-warp staging for the column-response build and the adjoint scatter
     float *yval = (float *)(smem + L.kst) + warp * 64;  // per-warp adjoint scatter staging
     // every band's samples stay in shared memory for the CTA's lifetime
-    const bool bands_staged = m.bands.k_total <= KTOT;
+    const bool bands_staged = TJ <= 8 && m.bands.k_total <= KTOT;
     if (bands_staged)
         for (int k = tid; k < m.bands.k_total; k += THREADS) {
             sLam[k] = __ldg(m.band_lam + k);
@@ -227,8 +231,14 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             }
             // per-lane accumulators with a fixed assignment (deterministic sums):
             // warp w owns sample w / WPS in the epilogue and the reverse dot
-            double chi_acc = 0.0;
-            float gacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // z(prefactor+phase), t0, x0, x1, c, z(lambda')
+            double chi_acc[SPW];
+            float gacc[SPW][6];  // z(prefactor+phase), t0, x0, x1, c, z(lambda')
+#pragma unroll
+            for (int jj = 0; jj < SPW; ++jj) {
+                chi_acc[jj] = 0.0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) gacc[jj][q] = 0.f;
+            }
 
             for (int64_t oc = 0; oc < nobs; oc += OBS_MAX) {
                 const int nc = (int)min((int64_t)OBS_MAX, nobs - oc);
@@ -307,7 +317,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     if (tid == 0) { sMisc[4] = 0x7fffffff; sMisc[5] = -1; sMisc[6] = 0; }
                     for (int q = tid; q < NPH_MAX / 32; q += THREADS) sRowMask[q] = 0u;
                     if (GRAD)
-                        for (int q = tid; q < WARPS * NP; q += THREADS) sYw[q] = 0.f;
+                        for (int q = tid; q < WARPS * SPW * NP; q += THREADS) sYw[q] = 0.f;
                     __syncthreads();
                     if (warp == 0 && lane < nj) {
                         const int j = lane;
@@ -387,8 +397,9 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         if (WPS > 1)
                             for (int q = tid; q < WARPS * WMAX; q += THREADS) sEp[q] = 0.f;
                         __syncthreads();
-                        {
-                            const int j = warp / WPS, sub = warp % WPS;
+#pragma unroll
+                        for (int jj = 0; jj < SPW; ++jj) {
+                            const int j = (warp / WPS) * SPW + jj, sub = warp % WPS;
                             if (j < nj && sPj[PJ_OK * TJ + j] != 0.f) {
                                 const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
                                 const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
@@ -443,14 +454,15 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     __syncthreads();
 
                     // ---- 3. epilogue per (observation, sample) pair; adjoint scatter
-                    {
-                        const int j = warp / WPS, sub = warp % WPS;
+#pragma unroll
+                    for (int jj = 0; jj < SPW; ++jj) {
+                        const int j = (warp / WPS) * SPW + jj, sub = warp % WPS;
                         if (j < nj) {
                             const bool okj = sPj[PJ_OK * TJ + j] != 0.f;
                             const float a = sPj[PJ_A * TJ + j], x0 = sPj[PJ_X0 * TJ + j];
                             const float x1 = sPj[PJ_X1 * TJ + j];
                             const double t0 = sT0[j];
-                            float *yw = sYw + warp * NP;
+                            float *yw = sYw + (warp * SPW + jj) * NP;
                             for (int base = sub * 32; base < nb_obs; base += 32 * WPS) {
                                 const int il = base + lane;
                                 const bool act = il < nb_obs;
@@ -484,13 +496,13 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     } else {
                                         const float sig = sSig[i];
                                         const float r = (sFlux[i] - B) / sig;
-                                        chi_acc = fma((double)r, (double)r, chi_acc);
+                                        chi_acc[jj] = fma((double)r, (double)r, chi_acc[jj]);
                                         if (GRAD) {
                                             const float g = -2.0f * r / sig;
-                                            gacc[0] += g * (-a * B - pre * a * p * Bp);
-                                            gacc[1] += g * pre * Bp * (-a);
-                                            gacc[2] += g * a * zpf * Bs;
-                                            gacc[3] += g * pre * B1;
+                                            gacc[jj][0] += g * (-a * B - pre * a * p * Bp);
+                                            gacc[jj][1] += g * pre * Bp * (-a);
+                                            gacc[jj][2] += g * a * zpf * Bs;
+                                            gacc[jj][3] += g * pre * B1;
                                             coef = g * pre;
                                         }
                                     }
@@ -564,14 +576,15 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             __syncthreads();
                             // adjoint of the column response per band sample: dchi2/dc and the
                             // rest-wavelength part of dchi2/dz (warp -> sample, band samples split by sub)
-                            {
-                                const int j = warp / WPS, sub = warp % WPS;
+#pragma unroll
+                            for (int jj = 0; jj < SPW; ++jj) {
+                                const int j = (warp / WPS) * SPW + jj, sub = warp % WPS;
                                 if (j < nj && sPj[PJ_OK * TJ + j] != 0.f) {
                                     const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
                                     const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                     const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
                                     eadjoint(m, lam, wk, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane, sQf + j, TJ,
-                                             gacc[4], gacc[5]);
+                                             gacc[jj][4], gacc[jj][5]);
                                 }
                             }
                         }
@@ -582,14 +595,18 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             // ---- per-sample reductions in a fixed order, outputs
             if (MODE != MODE_BANDFLUX) {
                 __syncthreads();
-                chi_acc = warp_sum_d(chi_acc);
-                float gr[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) gr[q] = GRAD ? warp_sum(gacc[q]) : 0.f;
-                if (lane == 0) {
-                    sRed[warp * 8 + 0] = chi_acc;
+                for (int jj = 0; jj < SPW; ++jj) {
+                    const double x2w = warp_sum_d(chi_acc[jj]);
+                    float gr[6];
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) sRed[warp * 8 + 1 + q] = gr[q];
+                    for (int q = 0; q < 6; ++q) gr[q] = GRAD ? warp_sum(gacc[jj][q]) : 0.f;
+                    if (lane == 0) {
+                        double *rd = sRed + (warp * SPW + jj) * 8;
+                        rd[0] = x2w;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) rd[1 + q] = gr[q];
+                    }
                 }
                 __syncthreads();
                 if (tid < nj) {
@@ -630,7 +647,7 @@ int factorised_smem_bytes(int tile, int mode) {
     return (int)fk::Lay(tile, mode == MODE_GRAD, fk::NPH_MAX).total;
 }
 
-int factorised_max_tile() { return 8; }
+int factorised_max_tile() { return 16; }
 
 template <int TJ, int MODE>
 static cudaError_t launch_fk(const salt_ctx *ctx, const WorkItem *items_d, int n_items, int *counter_d,
@@ -677,7 +694,8 @@ cudaError_t launch_factorised_items(const salt_ctx *ctx, int tile, const WorkIte
         case 1: return launch_fk_mode<1>(ctx, items_d, n_items, counter_d, b, o, mode, st);
         case 2: return launch_fk_mode<2>(ctx, items_d, n_items, counter_d, b, o, mode, st);
         case 4: return launch_fk_mode<4>(ctx, items_d, n_items, counter_d, b, o, mode, st);
-        default: return launch_fk_mode<8>(ctx, items_d, n_items, counter_d, b, o, mode, st);
+        case 8: return launch_fk_mode<8>(ctx, items_d, n_items, counter_d, b, o, mode, st);
+        default: return launch_fk_mode<16>(ctx, items_d, n_items, counter_d, b, o, mode, st);
     }
 }
 

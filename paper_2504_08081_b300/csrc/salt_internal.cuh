@@ -90,9 +90,9 @@ struct WorkItem {
 
 // Launch configurations of the factorised path: kernel family and tile.
 enum Family : int { FAM_CTA = 0, FAM_WARP = 1, FAM_UNIT = 2 };
-inline int cfg_key(int family, int tile) { return family * 16 + tile; }
-inline int cfg_family(int key) { return key / 16; }
-inline int cfg_tile(int key) { return key % 16; }
+inline int cfg_key(int family, int tile) { return family * 32 + tile; }  // tile <= 16
+inline int cfg_family(int key) { return key / 32; }
+inline int cfg_tile(int key) { return key % 32; }
 
 }  // namespace salt
 
@@ -143,7 +143,7 @@ struct salt_ctx {
     int tile_samples = 0;  // 0 = autotuned
     int use_graphs = 1;
     int serve_chunk = 64;
-    int last_kernel = 0;   // SALT_KERNEL_* x 16 + tile of the last batch launch (0 = none yet)
+    int last_kernel = 0;   // SALT_KERNEL_* x 32 + tile of the last batch launch (0 = none yet)
     cudaStream_t capture_stream = nullptr;  // private stream for graph capture (created on first use)
     std::vector<double> host_cl;  // colour-law coefficients (for serving validation)
     std::vector<float> host_lam, host_w;  // band tables as uploaded (for registering bands)

@@ -202,7 +202,7 @@ class Salt:
     def last_kernel(self) -> tuple[int, int]:
         """(SALT_KERNEL_* family, samples per tile) of the last batch launch."""
         v = self.ctx.get_option(_abi.SALT_OPT_LAST_KERNEL)
-        return v // 16, v % 16
+        return v // 32, v % 32
 
     # -- serving -------------------------------------------------------------
     def submit(self, n_obs, mjd, band, flux, fluxerr, zp, t0, z, x0, x1, c, want_grad) -> int:

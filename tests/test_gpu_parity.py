@@ -65,7 +65,7 @@ def test_bandflux_single_supernova(cfg1, kernel):
 
 
 @pytest.mark.parametrize("kernel", ["direct", "factorised", "bandwarp", "unit"])
-@pytest.mark.parametrize("tile", [1, 2, 4, 8])
+@pytest.mark.parametrize("tile", [1, 2, 4, 8, 16])
 def test_bandflux_and_chi2_batched(cfg2_sub, kernel, tile):
     wl, o = cfg2_sub
     bt = wl.batch
