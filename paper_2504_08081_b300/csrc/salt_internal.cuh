@@ -142,7 +142,7 @@ struct salt_ctx {
     int kernel = SALT_KERNEL_AUTO;
     int tile_samples = 0;  // 0 = autotuned
     int use_graphs = 1;
-    int serve_chunk = 64;
+    int serve_chunk = 8;  // samples per serving work item (latency: one 8-sample tile per item)
     int last_kernel = 0;   // SALT_KERNEL_* x 32 + tile of the last batch launch (0 = none yet)
     cudaStream_t capture_stream = nullptr;  // private stream for graph capture (created on first use)
     std::vector<double> host_cl;  // colour-law coefficients (for serving validation)

@@ -6,10 +6,14 @@
 // observation array (mjd, band, flux, fluxerr, zp) shares one element index
 // space and every sample array (t0, z, x0, x1, c, chi2, grad) another, so one
 // work item addresses a request's data with a single element offset. A
-// scheduler thread turns the admitted requests' fixed-size sample chunks into
-// one ragged work list per (mode, tile) and launches the fused factorised
-// kernel over it; requests that arrive while earlier launches run on the GPU
-// join the next one. Uploads, kernels and downloads run on three streams
+// scheduler thread turns the admitted requests' fixed-size sample chunks
+// (8 samples: one tile, so a request's items spread over many CTAs and finish
+// fast) into one ragged work list per (mode, tile) and launches the fused
+// factorised kernel over it; requests that arrive while earlier launches run
+// on the GPU join the next one, and with 8 launch groups in flight new
+// requests wait to be grouped into larger ones. A tick's admitted requests are
+// packed into a pinned staging buffer and uploaded with one copy per array and
+// one scatter kernel. Uploads, kernels and downloads run on three streams
 // ordered by events, so copies overlap other requests' kernels. A request's
 // chunks go through exactly the same per-item code whatever else shares the
 // launch, so its results are bitwise identical alone and in a mix.
@@ -108,6 +112,44 @@ constexpr int kMaxItems = 1 << 15;  // items per launch group
 constexpr size_t kObsBytes = 8 + 4 * 4;        // mjd, band, flux, fluxerr, zp
 constexpr size_t kParBytes = 8 + 4 * 4 + 8 + 20;  // t0, z, x0, x1, c, chi2, grad[5]
 
+// Upload staging: the requests admitted in one tick are packed into a pinned
+// buffer, copied with one transfer per array and scattered into the arenas by
+// one kernel (instead of ten small pageable copies per request). Two buffers
+// alternate so the host fills one while the other is in flight.
+constexpr size_t kStageObs = size_t(1) << 19;  // observations per staging buffer
+constexpr size_t kStagePar = size_t(1) << 19;  // samples per staging buffer
+constexpr int kStageReq = 8192;                // requests per staging buffer
+
+struct UpDesc {  // one request: where its rows sit in the staging buffer and in the arenas
+    int64_t src_obs, dst_obs, n_obs, src_par, dst_par, n_par;
+};
+
+struct StageLayout {  // byte offsets inside a staging buffer (host and device alike)
+    size_t mjd, t0, band, flux, fluxerr, zp, z, x0, x1, c, desc, total;
+    StageLayout() {
+        size_t o = 0;
+        auto take = [&](size_t bytes) { const size_t at = o; o += (bytes + 255) & ~size_t(255); return at; };
+        mjd = take(8 * kStageObs);
+        t0 = take(8 * kStagePar);
+        band = take(4 * kStageObs);
+        flux = take(4 * kStageObs);
+        fluxerr = take(4 * kStageObs);
+        zp = take(4 * kStageObs);
+        z = take(4 * kStagePar);
+        x0 = take(4 * kStagePar);
+        x1 = take(4 * kStagePar);
+        c = take(4 * kStagePar);
+        desc = take(sizeof(UpDesc) * kStageReq);
+        total = o;
+    }
+};
+
+struct Stage {
+    unsigned char *h = nullptr, *d = nullptr;
+    cudaEvent_t ev = nullptr;  // the last upload from this buffer has finished
+    bool busy = false;
+};
+
 }  // namespace
 
 struct ServeEngine {
@@ -126,9 +168,16 @@ struct ServeEngine {
     WorkItem *items_h[kSlots] = {};
     int *counters_d = nullptr;
     bool slot_busy[kSlots] = {};
+    Stage stage[2];
+    int stage_cur = 0;
+    StageLayout SL;
+    int max_inflight = 8;  // launch groups in flight before new requests wait to be grouped
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
+    // requests by state, so a tick touches only what can change
+    std::vector<uint64_t> pending[2][4];  // admitted, not launched: [chi2 / grad][tile 1, 2, 4, 8]
+    std::vector<uint64_t> copying;        // results on their way to the host
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     std::list<Launch> inflight;
     std::vector<double> lat_ms;
@@ -156,6 +205,40 @@ void release_req(ServeEngine *e, Req &r) {
     r.oo = r.po = SIZE_MAX;
     if (r.ev_down) cudaEventDestroy(r.ev_down);
     r.ev_down = nullptr;
+}
+
+// Scatter one tick's staged requests into the arenas: thread per row.
+__global__ void k_stage_scatter(const unsigned char *stg, StageLayout L, int n_desc, int64_t n_obs, int64_t n_par,
+                                double *mjd, int32_t *band, float *flux, float *fluxerr, float *zp, double *t0,
+                                float *z, float *x0, float *x1, float *c) {
+    const UpDesc *d = (const UpDesc *)(stg + L.desc);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += stride) {
+        int lo = 0, hi = n_desc;  // the last request whose rows start at or before i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (d[mid].src_obs <= i) lo = mid; else hi = mid;
+        }
+        const int64_t o = d[lo].dst_obs + (i - d[lo].src_obs);
+        mjd[o] = ((const double *)(stg + L.mjd))[i];
+        band[o] = ((const int32_t *)(stg + L.band))[i];
+        flux[o] = ((const float *)(stg + L.flux))[i];
+        fluxerr[o] = ((const float *)(stg + L.fluxerr))[i];
+        zp[o] = ((const float *)(stg + L.zp))[i];
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_par; i += stride) {
+        int lo = 0, hi = n_desc;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (d[mid].src_par <= i) lo = mid; else hi = mid;
+        }
+        const int64_t q = d[lo].dst_par + (i - d[lo].src_par);
+        t0[q] = ((const double *)(stg + L.t0))[i];
+        z[q] = ((const float *)(stg + L.z))[i];
+        x0[q] = ((const float *)(stg + L.x0))[i];
+        x1[q] = ((const float *)(stg + L.x1))[i];
+        c[q] = ((const float *)(stg + L.c))[i];
+    }
 }
 
 int tile_for(int n_par) {
@@ -199,17 +282,20 @@ bool tick(ServeEngine *e) {
             if (err == cudaSuccess) err = cudaEventRecord(r.ev_down, e->s_down);
             if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
             r.st = St::COPYING;
+            e->copying.push_back(r.ticket);
         }
         cudaEventDestroy(it->ev);
         e->slot_busy[it->slot] = false;
         it = e->inflight.erase(it);
     }
     // 2. finished downloads -> results to the request, release its arena ranges
-    for (auto &kv : e->reqs) {
-        Req &r = *kv.second;
-        if (r.st != St::COPYING) continue;
+    size_t keep = 0;
+    for (size_t qi = 0; qi < e->copying.size(); ++qi) {
+        auto rq = e->reqs.find(e->copying[qi]);
+        if (rq == e->reqs.end() || rq->second->st != St::COPYING) continue;
+        Req &r = *rq->second;
         err = cudaEventQuery(r.ev_down);
-        if (err == cudaErrorNotReady) continue;
+        if (err == cudaErrorNotReady) { e->copying[keep++] = e->copying[qi]; continue; }
         if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
         r.t_done = now_ms();
         r.chi2.assign(e->h_chi2 + r.po, e->h_chi2 + r.po + r.n_par);
@@ -222,36 +308,100 @@ bool tick(ServeEngine *e) {
         }
         e->cv_done.notify_all();
     }
-    // 3. admit queued requests while both arenas have room (FIFO)
+    e->copying.resize(keep);
+    // 3. admit queued requests while both arenas (and the staging buffer) have room (FIFO)
+    Stage *sg = nullptr;
+    for (int t = 0; t < 2 && !sg; ++t) {
+        Stage &c = e->stage[(e->stage_cur + t) & 1];
+        if (c.busy) {
+            err = cudaEventQuery(c.ev);
+            if (err == cudaErrorNotReady) continue;
+            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+            c.busy = false;
+        }
+        sg = &c;
+        e->stage_cur = (e->stage_cur + t) & 1;
+    }
+    const StageLayout &SL = e->SL;
+    size_t so = 0, sp = 0;  // staged observations / samples this tick
+    int nd = 0;
     bool uploaded = false;
     while (!e->queue.empty()) {
         auto rq = e->reqs.find(e->queue.front());
         if (rq == e->reqs.end() || rq->second->st != St::QUEUED) { e->queue.pop_front(); continue; }
         Req &r = *rq->second;
+        // requests larger than a staging buffer go straight to the arenas
+        const bool direct = (size_t)r.n_obs > kStageObs || (size_t)r.n_par > kStagePar;
+        if (!direct && (!sg || so + r.n_obs > kStageObs || sp + r.n_par > kStagePar || nd >= kStageReq)) break;
         size_t oo = SIZE_MAX, po = SIZE_MAX;
         if (!e->par_a.alloc((size_t)r.n_par, po)) break;
         if (!e->obs_a.alloc((size_t)r.n_obs, oo)) { e->par_a.release(po, (size_t)r.n_par); break; }
         r.oo = oo;
         r.po = po;
-        // pageable sources: each copy is staged by the driver before the call returns
-        err = up(e->d_mjd, r.mjd, oo, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_band, r.band, oo, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_flux, r.flux, oo, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_fluxerr, r.fluxerr, oo, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_zp, r.zp, oo, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_t0, r.t0, po, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_z, r.z, po, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_x0, r.x0, po, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_x1, r.x1, po, e->s_up);
-        if (err == cudaSuccess) err = up(e->d_c, r.c, po, e->s_up);
-        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+        if (direct) {
+            // pageable sources: each copy is staged by the driver before the call returns
+            err = up(e->d_mjd, r.mjd, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_band, r.band, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_flux, r.flux, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_fluxerr, r.fluxerr, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_zp, r.zp, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_t0, r.t0, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_z, r.z, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_x0, r.x0, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_x1, r.x1, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_c, r.c, po, e->s_up);
+            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+        } else {
+            unsigned char *h = sg->h;
+            auto put = [&](size_t base, size_t at, const void *src, size_t bytes) {
+                if (bytes) std::memcpy(h + base + at, src, bytes);
+            };
+            put(SL.mjd, 8 * so, r.mjd.data(), 8 * (size_t)r.n_obs);
+            put(SL.band, 4 * so, r.band.data(), 4 * (size_t)r.n_obs);
+            put(SL.flux, 4 * so, r.flux.data(), 4 * (size_t)r.n_obs);
+            put(SL.fluxerr, 4 * so, r.fluxerr.data(), 4 * (size_t)r.n_obs);
+            put(SL.zp, 4 * so, r.zp.data(), 4 * (size_t)r.n_obs);
+            put(SL.t0, 8 * sp, r.t0.data(), 8 * (size_t)r.n_par);
+            put(SL.z, 4 * sp, r.z.data(), 4 * (size_t)r.n_par);
+            put(SL.x0, 4 * sp, r.x0.data(), 4 * (size_t)r.n_par);
+            put(SL.x1, 4 * sp, r.x1.data(), 4 * (size_t)r.n_par);
+            put(SL.c, 4 * sp, r.c.data(), 4 * (size_t)r.n_par);
+            UpDesc *dsc = (UpDesc *)(h + SL.desc);
+            dsc[nd++] = UpDesc{(int64_t)so, (int64_t)oo, r.n_obs, (int64_t)sp, (int64_t)po, r.n_par};
+            so += r.n_obs;
+            sp += r.n_par;
+        }
         std::vector<double>().swap(r.mjd);
         std::vector<double>().swap(r.t0);
         std::vector<int32_t>().swap(r.band);
         for (auto *v : {&r.flux, &r.fluxerr, &r.zp, &r.z, &r.x0, &r.x1, &r.c}) std::vector<float>().swap(*v);
         r.st = St::ACTIVE;
+        e->pending[r.grad ? 1 : 0][r.tile == 1 ? 0 : r.tile == 2 ? 1 : r.tile == 4 ? 2 : 3].push_back(r.ticket);
         uploaded = true;
         e->queue.pop_front();
+    }
+    if (nd > 0) {
+        // one transfer per array (used prefix) and one scatter kernel for the whole tick
+        const size_t parts[][2] = {{SL.mjd, 8 * so}, {SL.band, 4 * so}, {SL.flux, 4 * so},
+                                   {SL.fluxerr, 4 * so}, {SL.zp, 4 * so}, {SL.t0, 8 * sp},
+                                   {SL.z, 4 * sp}, {SL.x0, 4 * sp}, {SL.x1, 4 * sp},
+                                   {SL.c, 4 * sp}, {SL.desc, sizeof(UpDesc) * (size_t)nd}};
+        err = cudaSuccess;
+        for (const auto &pt : parts)
+            if (err == cudaSuccess && pt[1])
+                err = cudaMemcpyAsync(sg->d + pt[0], sg->h + pt[0], pt[1], cudaMemcpyHostToDevice, e->s_up);
+        if (err == cudaSuccess) {
+            const int64_t rows = (int64_t)std::max(so, sp);
+            const int blocks = (int)std::min<int64_t>((rows + 255) / 256, 4 * (int64_t)e->ctx->num_sms);
+            k_stage_scatter<<<std::max(blocks, 1), 256, 0, e->s_up>>>(
+                sg->d, SL, nd, (int64_t)so, (int64_t)sp, e->d_mjd, e->d_band, e->d_flux, e->d_fluxerr, e->d_zp,
+                e->d_t0, e->d_z, e->d_x0, e->d_x1, e->d_c);
+            err = cudaGetLastError();
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(sg->ev, e->s_up);
+        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+        sg->busy = true;
+        e->stage_cur ^= 1;
     }
     if (uploaded) {
         err = cudaEventRecord(e->ev_up, e->s_up);
@@ -265,31 +415,40 @@ bool tick(ServeEngine *e) {
     b.t0 = e->d_t0; b.z = e->d_z; b.x0 = e->d_x0; b.x1 = e->d_x1; b.c = e->d_c;
     OutDev o{nullptr, nullptr, e->d_chi2, e->d_grad, e->ctx->err_d};
     for (int mode = MODE_CHI2; mode <= MODE_GRAD; ++mode) {
-        for (int tile : {1, 2, 4, 8}) {
+        for (int ti = 0; ti < 4; ++ti) {
+            const int tile = 1 << ti;
+            std::vector<uint64_t> &bucket = e->pending[mode == MODE_GRAD ? 1 : 0][ti];
+            if (bucket.empty()) continue;
+            // while enough launches keep the GPU busy, let requests gather into larger ones
+            if ((int)e->inflight.size() >= e->max_inflight) return true;
             int slot = -1;
             for (int q = 0; q < kSlots; ++q)
                 if (!e->slot_busy[q]) { slot = q; break; }
             if (slot < 0) return true;  // all item buffers in flight: next tick
-            std::vector<uint64_t> members;
+            std::vector<uint64_t> members, later;
             int n_items = 0;
-            for (auto &kv : e->reqs) {
-                Req &r = *kv.second;
+            for (uint64_t t : bucket) {
+                auto rq = e->reqs.find(t);
+                if (rq == e->reqs.end()) continue;
+                Req &r = *rq->second;
                 if (r.st != St::ACTIVE || r.launched || r.cancel) continue;
-                if ((r.grad ? MODE_GRAD : MODE_CHI2) != mode || r.tile != tile) continue;
-                const int need = (r.n_par + chunk - 1) / chunk;
-                if (n_items + need > kMaxItems) continue;
-                for (int j0 = 0; j0 < r.n_par; j0 += chunk) {
+                // a request too large for one item list takes larger chunks
+                const int cr = std::max(chunk, (r.n_par + kMaxItems - 1) / kMaxItems);
+                const int need = (r.n_par + cr - 1) / cr;
+                if (n_items + need > kMaxItems) { later.push_back(t); continue; }
+                for (int j0 = 0; j0 < r.n_par; j0 += cr) {
                     WorkItem w{};
                     w.obs0 = (int64_t)r.oo;
                     w.par0 = (int64_t)r.po + j0;
                     w.bf0 = 0;
                     w.nobs = r.n_obs;
-                    w.nj = std::min(chunk, r.n_par - j0);
+                    w.nj = std::min(cr, r.n_par - j0);
                     w.jloc0 = j0;
                     e->items_h[slot][n_items++] = w;
                 }
                 members.push_back(r.ticket);
             }
+            bucket.swap(later);
             if (members.empty()) continue;
             Launch L;
             L.slot = slot;
@@ -316,11 +475,10 @@ bool tick(ServeEngine *e) {
 }
 
 bool has_work(ServeEngine *e) {
-    if (!e->inflight.empty() || !e->queue.empty()) return true;
-    for (auto &kv : e->reqs) {
-        const Req &r = *kv.second;
-        if (r.st == St::COPYING || (r.st == St::ACTIVE && !r.launched)) return true;
-    }
+    if (!e->inflight.empty() || !e->queue.empty() || !e->copying.empty()) return true;
+    for (auto &mode : e->pending)
+        for (auto &bucket : mode)
+            if (!bucket.empty()) return true;
     return false;
 }
 
@@ -371,6 +529,11 @@ ServeEngine *serve_create(salt_ctx *ctx, size_t mem_limit) {
     if (ok) ok = cudaStreamCreateWithFlags(&e->s_comp, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) ok = cudaStreamCreateWithFlags(&e->s_down, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) ok = cudaEventCreateWithFlags(&e->ev_up, cudaEventDisableTiming) == cudaSuccess;
+    for (int q = 0; ok && q < 2; ++q) {
+        dm((void **)&e->stage[q].d, e->SL.total);
+        if (ok) ok = cudaHostAlloc(&e->stage[q].h, e->SL.total, cudaHostAllocDefault) == cudaSuccess;
+        if (ok) ok = cudaEventCreateWithFlags(&e->stage[q].ev, cudaEventDisableTiming) == cudaSuccess;
+    }
     for (int q = 0; ok && q < kSlots; ++q) {
         dm((void **)&e->items_d[q], kMaxItems * sizeof(WorkItem));
         if (ok) ok = cudaHostAlloc(&e->items_h[q], kMaxItems * sizeof(WorkItem), cudaHostAllocDefault) == cudaSuccess;
@@ -401,6 +564,11 @@ void serve_destroy(ServeEngine *e) {
     for (int q = 0; q < kSlots; ++q) {
         if (e->items_d[q]) cudaFree(e->items_d[q]);
         if (e->items_h[q]) cudaFreeHost(e->items_h[q]);
+    }
+    for (auto &sg : e->stage) {
+        if (sg.d) cudaFree(sg.d);
+        if (sg.h) cudaFreeHost(sg.h);
+        if (sg.ev) cudaEventDestroy(sg.ev);
     }
     void *dptrs[] = {e->d_mjd, e->d_band, e->d_flux, e->d_fluxerr, e->d_zp, e->d_t0, e->d_z, e->d_x0,
                      e->d_x1, e->d_c, e->d_chi2, e->d_grad, e->counters_d};

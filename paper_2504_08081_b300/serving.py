@@ -22,34 +22,59 @@ def _req_arrays(rq):
                 t0=b.t0, z=b.z, x0=b.x0, x1=b.x1, c=b.c, want_grad=rq.want_grad)
 
 
+def _prepared(requests):
+    """ctypes request descriptors and result buffers built ahead of the replay,
+    so the timed loops only call into the library."""
+    import ctypes as C
+    out = []
+    for rq in requests:
+        b = rq.batch
+        arrs = [np.ascontiguousarray(b.mjd, np.float64), np.ascontiguousarray(b.band, np.int32),
+                np.ascontiguousarray(b.flux, np.float32), np.ascontiguousarray(b.fluxerr, np.float32),
+                np.ascontiguousarray(b.zp, np.float32), np.ascontiguousarray(b.t0, np.float64),
+                np.ascontiguousarray(b.z, np.float32), np.ascontiguousarray(b.x0, np.float32),
+                np.ascontiguousarray(b.x1, np.float32), np.ascontiguousarray(b.c, np.float32)]
+        req = _abi.Request(int(b.n_obs), len(arrs[5]), 1 if rq.want_grad else 0, *[a.ctypes.data for a in arrs])
+        chi2 = np.empty(b.n_par, np.float64)
+        grad = np.empty((b.n_par, 5), np.float32) if rq.want_grad else None
+        out.append((req, arrs, chi2, grad, C.c_uint64()))
+    return out
+
+
 def replay(salt: Salt, requests, arrivals_s=None, collect=True):
     """Submit requests (at their arrival times when given, else all at once),
-    wait for every result. Returns (wall seconds, results list, stats dict)."""
+    wait for every result. Request descriptors and result buffers are built
+    before the clock starts; the submitting and the polling thread then only
+    call into the library (ctypes releases the interpreter lock meanwhile).
+    Returns (wall seconds, results list, stats dict)."""
+    import ctypes as C
     n = len(requests)
+    prep = _prepared(requests)
+    L = _abi.lib()
+    h = salt.ctx.h
     tickets = [None] * n
-    results = [None] * n
-    done = threading.Event()
     errors = []
+    abort = [False]
 
     def poller():
         try:
             for i in range(n):
                 while tickets[i] is None:
+                    if abort[0]:
+                        return
                     time.sleep(0)
-                rq = requests[i]
-                rc, x2, g = salt.poll(tickets[i], rq.batch.n_par, rq.want_grad, wait_ms=-1)
+                _, _, chi2, grad, _ = prep[i]
+                rc = L.salt_serve_poll(h, tickets[i], -1, chi2.ctypes.data,
+                                       grad.ctypes.data if grad is not None else None)
                 if rc != _abi.SALT_OK:
                     errors.append((i, rc))
-                if collect:
-                    results[i] = (x2, g)
         except Exception as ex:  # pragma: no cover - surfaced below
             errors.append(("poller", repr(ex)))
-        done.set()
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
     t0 = time.perf_counter()
-    for i, rq in enumerate(requests):
+    for i in range(n):
         if arrivals_s is not None:
             target = t0 + arrivals_s[i]
             while True:
@@ -58,12 +83,18 @@ def replay(salt: Salt, requests, arrivals_s=None, collect=True):
                     break
                 if dt > 2e-4:
                     time.sleep(dt - 1e-4)
-        tickets[i] = salt.submit(**_req_arrays(rq))
-    done.wait()
-    wall = time.perf_counter() - t0
+        req, _, _, _, tk = prep[i]
+        rc = L.salt_serve_submit(h, C.byref(req), C.byref(tk))
+        if rc != _abi.SALT_OK:
+            errors.append((i, rc))
+            abort[0] = True
+            break
+        tickets[i] = tk.value
     th.join()
+    wall = time.perf_counter() - t0
     if errors:
         raise RuntimeError(f"serving errors: {errors[:5]}")
+    results = [(p[2], p[3]) for p in prep] if collect else [None] * n
     return wall, results, salt.serve_stats()
 
 
