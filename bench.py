@@ -536,6 +536,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "chi2_grad_evals_per_s": n_par_all / (ms_max / 1e3),
+        "ms_per_step_median": statistics.median(durs), "ms_per_step_min": min(durs),
         "sync_call_ms": sync_ms,
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
