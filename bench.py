@@ -153,6 +153,11 @@ class ClockSampler:
             self._t.start()
         except Exception:
             self.proc = None
+        # nvidia-smi's start-up (driver queries before its first sample) disturbs
+        # the first milliseconds of GPU work: begin timing after its first sample
+        t_end = time.perf_counter() + 5.0
+        while self.proc is not None and not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.01)
         time.sleep(0.25)
         return self
 
@@ -250,6 +255,70 @@ def reduce_over_ranks(ms, n_bandflux, n_par, device):
     return float(ms_t.item()), float(cnt[0].item()), float(cnt[1].item())
 
 
+def time_steps_graph(fn, steps, warmup, stream, flush=None):
+    """Device time of each step with no host work inside the timed region:
+    the K steps (L2 flush, event, step, event) are captured once into one CUDA
+    graph, whose event nodes record on the stream, and the graph is launched
+    once; one synchronize on each side. Returns None when the capture cannot be
+    made (the caller then falls back to time_steps)."""
+    import torch
+    try:
+        from cuda.bindings import runtime as rt
+    except ImportError:
+        return None
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = rt.cudaStream_t(stream.cuda_stream)
+    evs = []
+    for _ in range(2 * steps):
+        err, ev = rt.cudaEventCreate()
+        if err != rt.cudaError_t.cudaSuccess:
+            return None
+        evs.append(ev)
+    graph = exec_ = None
+    try:
+        if rt.cudaStreamBeginCapture(st, rt.cudaStreamCaptureMode.cudaStreamCaptureModeThreadLocal)[0] != \
+                rt.cudaError_t.cudaSuccess:
+            return None
+        ok = True
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                if flush is not None:
+                    flush()
+                ok &= rt.cudaEventRecordWithFlags(evs[2 * i], st, rt.cudaEventRecordExternal)[0] == \
+                    rt.cudaError_t.cudaSuccess
+                fn()
+                ok &= rt.cudaEventRecordWithFlags(evs[2 * i + 1], st, rt.cudaEventRecordExternal)[0] == \
+                    rt.cudaError_t.cudaSuccess
+        err, graph = rt.cudaStreamEndCapture(st)
+        if err != rt.cudaError_t.cudaSuccess or not ok:
+            return None
+        err, exec_ = rt.cudaGraphInstantiate(graph, 0)
+        if err != rt.cudaError_t.cudaSuccess:
+            return None
+        # one untimed replay (first launch of a graph uploads it), then the timed one
+        for rep in range(2):
+            torch.cuda.synchronize()
+            if rt.cudaGraphLaunch(exec_, st)[0] != rt.cudaError_t.cudaSuccess:
+                return None
+            torch.cuda.synchronize()
+        durs = []
+        for i in range(steps):
+            err, ms = rt.cudaEventElapsedTime(evs[2 * i], evs[2 * i + 1])
+            if err != rt.cudaError_t.cudaSuccess:
+                return None
+            durs.append(ms)
+        return durs
+    finally:
+        if exec_ is not None:
+            rt.cudaGraphExecDestroy(exec_)
+        if graph is not None:
+            rt.cudaGraphDestroy(graph)
+        for ev in evs:
+            rt.cudaEventDestroy(ev)
+
+
 def time_steps(fn, steps, warmup, stream, flush=None, queue_ahead=True):
     """Device time of each step: a pair of CUDA events on `stream` around it,
     the L2 flush (if any) enqueued before the first event. With queue_ahead
@@ -264,9 +333,9 @@ def time_steps(fn, steps, warmup, stream, flush=None, queue_ahead=True):
     if queue_ahead:
         with torch.cuda.stream(stream):
             torch.cuda._sleep(int(4e6) * max(1, steps // 5))  # ~2 ms per 5 steps at 2 GHz
-        # two untimed steps queued behind the spin bring the clocks back up
-        # before the first timed step (the one-thread spin lets them drop)
-        for _ in range(2):
+        # untimed steps queued behind the spin bring the clocks back up before
+        # the first timed step (the one-thread spin and the idle host let them drop)
+        for _ in range(10):
             if flush is not None:
                 flush()
             fn()
@@ -447,7 +516,11 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         with ClockSampler(local_rank) as clk:
             t_wall = time.perf_counter()
-            durs = time_steps(step, args.steps, 0, stream, flush=flush_buf.zero_)
+            durs = time_steps_graph(step, args.steps, 0, stream, flush=flush_buf.zero_)
+            timing = "one CUDA graph of the K steps (flush, event, step, event), launched once"
+            if durs is None:
+                durs = time_steps(step, args.steps, 0, stream, flush=flush_buf.zero_)
+                timing = "per-step events, steps queued behind a device-side spin"
             torch.cuda.synchronize()
             t_wall = time.perf_counter() - t_wall
         barrier()
@@ -465,21 +538,36 @@ def run_ours(args, rank, world, local_rank):
     ms_max, n_bf_all, n_par_all = reduce_over_ranks(ms, bt.n_bandflux(), bt.n_par, dev)
     value = n_bf_all / (ms_max / 1e3)
 
-    # ---- end to end through the public API: pinned host inputs -> device -> host results
+    # ---- end to end through the public API: pinned host inputs -> device -> host results.
+    # The ten input arrays live in one pinned host buffer (each 256-byte aligned)
+    # and go up in one transfer; the device batch views the same layout. Results
+    # come back in one transfer per output.
     obs_names = ["mjd", "band", "flux", "fluxerr", "zp"]
     par_names = ["t0", "z", "x0", "x1", "c"]
-    host = {k: db.t[k].cpu().pin_memory() for k in obs_names + par_names}
+    src = {k: db.t[k].cpu() for k in obs_names + par_names}
+    offs, total = {}, 0
+    for k, v in src.items():
+        offs[k] = total
+        total += (v.numel() * v.element_size() + 255) // 256 * 256
+    host_buf = torch.empty(total, dtype=torch.uint8).pin_memory()
+    dev_buf = torch.empty(total, dtype=torch.uint8, device=dev)
+
+    def view(buf, k):
+        v = src[k]
+        return buf[offs[k]:offs[k] + v.numel() * v.element_size()].view(v.dtype)
+
+    for k in src:
+        view(host_buf, k).copy_(src[k])
     chi2_h = torch.empty(bt.n_par, dtype=torch.float64).pin_memory()
     grad_h = torch.empty((bt.n_par, 5), dtype=torch.float32).pin_memory()
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = total
     d2h = chi2_h.numel() * 8 + grad_h.numel() * 4
-    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    dev_in = {k: view(dev_buf, k) for k in src}
     from paper_2504_08081_b300.torch_api import DeviceBatch
     db2 = DeviceBatch(db.obs_off, db.par_off, dev_in, db.plan)
 
     def e2e_step():
-        for k in host:
-            dev_in[k].copy_(host[k], non_blocking=True)
+        dev_buf.copy_(host_buf, non_blocking=True)
         salt.chi2_grad(db2, chi2, grad)
         chi2_h.copy_(chi2, non_blocking=True)
         grad_h.copy_(grad, non_blocking=True)
@@ -534,9 +622,11 @@ def run_ours(args, rank, world, local_rank):
                    "bands": len(wl.bands), "grid": [wl.model.n_phase, wl.model.n_wave],
                    "step": "salt_chi2_grad (chi2 + adjoint gradient)",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "timing": timing,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "chi2_grad_evals_per_s": n_par_all / (ms_max / 1e3),
         "ms_per_step_median": statistics.median(durs), "ms_per_step_min": min(durs),
+        "ms_per_step_all": [round(d, 4) for d in durs],
         "sync_call_ms": sync_ms,
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -323,7 +323,10 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         const int j = lane;
                         const float a = sPj[PJ_A * TJ + j];
                         int kf = K, kl = -1;
-                        if (sPj[PJ_OK * TJ + j] != 0.f) {
+                        if (sPj[PJ_OK * TJ + j] != 0.f && lam[0] * a >= m.wave0 && lam[K - 1] * a <= m.wave_max) {
+                            kf = 0;  // lambda ascending: both ends inside means every sample is
+                            kl = K - 1;
+                        } else if (sPj[PJ_OK * TJ + j] != 0.f) {
                             // first k with a*lambda_k >= wave0; last with a*lambda_k <= wave_max
                             int lo = 0, hi = K;
                             while (lo < hi) { const int md = (lo + hi) >> 1; if (lam[md] * a >= m.wave0) hi = md; else lo = md + 1; }
