@@ -397,7 +397,8 @@ static int build_items(salt_ctx *ctx, salt_plan *p, int key, cudaStream_t st) {
 
 void plan_free(salt_plan *p, cudaStream_t st) {
     for (auto &kv : p->graphs)
-        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto &G : kv.second.e)
+            if (G.exec) cudaGraphExecDestroy(G.exec);
     p->graphs.clear();
     std::vector<void *> ptrs = {p->obs_off_d, p->par_off_d, p->bf_off_d, p->counter_d};
     for (auto &kv : p->lists) {
@@ -523,10 +524,11 @@ static int tune(salt_ctx *ctx, salt_plan *p, const BatchDev &b, const OutDev &o,
 }
 
 // Graph replay for repeated plan calls. A call whose batch and output pointers
-// equal the previous call's (same mode and configuration) is captured once on
-// the context's private stream (the launch's counter reset and kernel become a
-// two-node graph) and replayed on the caller's stream from then on; a call with
-// new pointers launches directly and drops the stale graph. Returns false when
+// equal those of an earlier call (same mode and configuration; up to
+// kGraphSlots pointer sets are remembered) is captured once on the context's
+// private stream (the launch's counter reset and kernel become a two-node
+// graph) and replayed on the caller's stream from then on; a call with new
+// pointers launches directly and takes the least recently used slot. Returns false when
 // the caller should launch directly (never while the caller's stream is
 // capturing: the caller's own graph then records the direct launch).
 static bool replay_graph(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b, const OutDev &o, int mode,
@@ -536,22 +538,37 @@ static bool replay_graph(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b
         (void)cudaGetLastError();
         return false;
     }
-    salt_plan::GraphEntry &G = p->graphs[mode * 256 + key];
-    if (G.failed) return false;
-    const bool same = G.seen && std::memcmp(&G.b, &b, sizeof b) == 0 && std::memcmp(&G.o, &o, sizeof o) == 0;
-    if (!same) {
-        if (G.exec) cudaGraphExecDestroy(G.exec);
-        G.exec = nullptr;
-        G.b = b;
-        G.o = o;
-        G.seen = true;
+    salt_plan::GraphSet &S = p->graphs[mode * 256 + key];
+    if (S.failed) return false;
+    salt_plan::GraphEntry *G = nullptr;
+    for (auto &x : S.e)
+        if (x.seen && std::memcmp(&x.b, &b, sizeof b) == 0 && std::memcmp(&x.o, &o, sizeof o) == 0) {
+            G = &x;
+            break;
+        }
+    if (!G) {  // a new pointer set: record it in a free slot, else the least recently used one
+        salt_plan::GraphEntry *v = &S.e[0];
+        for (auto &x : S.e) {
+            if (!x.seen) {
+                v = &x;
+                break;
+            }
+            if (x.used < v->used) v = &x;
+        }
+        if (v->exec) cudaGraphExecDestroy(v->exec);
+        v->exec = nullptr;
+        v->b = b;
+        v->o = o;
+        v->seen = true;
+        v->used = ++S.tick;
         return false;
     }
-    if (!G.exec) {
+    G->used = ++S.tick;
+    if (!G->exec) {
         if (!ctx->capture_stream &&
             cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
             (void)cudaGetLastError();
-            G.failed = true;
+            S.failed = true;
             return false;
         }
         cudaGraph_t g = nullptr;
@@ -561,16 +578,16 @@ static bool replay_graph(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b
             e = cudaStreamEndCapture(ctx->capture_stream, &g);
             if (el != cudaSuccess) e = el;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            G.exec = nullptr;
-            G.failed = true;
+            G->exec = nullptr;
+            S.failed = true;
             return false;
         }
     }
-    *err = cudaGraphLaunch(G.exec, st);
+    *err = cudaGraphLaunch(G->exec, st);
     return true;
 }
 
@@ -578,7 +595,8 @@ static bool replay_graph(salt_ctx *ctx, salt_plan *p, int key, const BatchDev &b
 // choices; the offsets stay. Used when the context's bands changed.
 static void plan_reset_work(salt_plan *p) {
     for (auto &kv : p->graphs)
-        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto &G : kv.second.e)
+            if (G.exec) cudaGraphExecDestroy(G.exec);
     p->graphs.clear();
     for (auto &kv : p->lists) {
         if (kv.second.d) cudaFree(kv.second.d);

@@ -113,17 +113,25 @@ struct salt_plan {
     int band_gen = 0;               // the context's band generation the work state was built for
     int *counter_d = nullptr;      // dynamic work counter of the persistent kernels
     bool temporary = false;
-    // Captured CUDA graphs, one per (mode, launch configuration): the batch and
-    // output pointers of the last direct launch, and the graph captured once
-    // the same pointers came back.
+    // Captured CUDA graphs per (mode, launch configuration), for up to kGraphSlots
+    // sets of batch and output pointers (a caller alternating buffers keeps
+    // every set): a set's first call launches directly and records its pointers,
+    // the graph is captured when the same pointers come back, and the least
+    // recently used set makes room for a new one.
+    static constexpr int kGraphSlots = 4;
     struct GraphEntry {
         salt::BatchDev b{};
         salt::OutDev o{};
-        bool seen = false;     // b/o hold the last call's pointers
-        bool failed = false;   // capture failed once: launch directly from then on
+        bool seen = false;     // b/o hold a call's pointers
+        uint64_t used = 0;     // last use (set tick)
         cudaGraphExec_t exec = nullptr;
     };
-    std::map<int, GraphEntry> graphs;
+    struct GraphSet {
+        GraphEntry e[kGraphSlots];
+        bool failed = false;   // a capture failed once: launch directly from then on
+        uint64_t tick = 0;
+    };
+    std::map<int, GraphSet> graphs;
 };
 
 namespace salt {

@@ -63,3 +63,37 @@ def test_graph_replay_follows_new_output_pointers():
     for x, _ in outs[1:]:
         np.testing.assert_array_equal(x, outs[0][0])
     assert np.all(np.isfinite(outs[0][0]))
+
+
+@pytest.mark.parametrize("n_sets", [2, 4, 6])
+def test_graph_replay_with_alternating_buffer_sets(n_sets):
+    """A caller cycling through several input/output buffer sets (double
+    buffering) gets, call for call, what direct launches give; up to four sets
+    keep their captured graphs, more evict the least recently used one."""
+    wl = W.config2(n_sn=40)
+    H.with_oracle_flux(wl)
+    s = _salt(wl)
+    from paper_2504_08081_b300.torch_api import DeviceBatch
+    db = s.upload(wl.batch)
+    sets = []
+    for _ in range(n_sets):
+        t = {k: v.clone() for k, v in db.t.items()}
+        sets.append((DeviceBatch(db.obs_off, db.par_off, t, db.plan),
+                     torch.empty(db.n_par, dtype=torch.float64, device=s.device),
+                     torch.empty((db.n_par, 5), dtype=torch.float32, device=s.device)))
+    z0 = db.t["z"].clone()
+    results = {}
+    for graphs in (False, True):
+        s.set_graphs(graphs)
+        out = []
+        for call in range(4 * n_sets):
+            b, x2, g = sets[call % n_sets]
+            b.t["z"].copy_(z0 + 1e-4 * call)
+            s.chi2_grad(b, x2, g)
+            out.append((x2.cpu().numpy().copy(), g.cpu().numpy().copy()))
+        s.check()
+        results[graphs] = out
+    for (xa, ga), (xb, gb) in zip(results[False], results[True]):
+        np.testing.assert_array_equal(xa, xb)
+        np.testing.assert_array_equal(ga, gb)
+    assert not np.array_equal(results[True][-1][0], results[True][-2][0])
