@@ -356,6 +356,41 @@ def time_steps(fn, steps, warmup, stream, flush=None, queue_ahead=True):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def sampled_oracle(wl, s, db, stream, n_picks):
+    """The oracle on sampled (supernova, sample) pairs of a batch too large for
+    it: its rate on those pairs, and the error of this library's full-batch
+    results at those pairs against it."""
+    import torch
+    import oracle
+    bt = wl.batch
+    rng = np.random.default_rng(77)
+    picks = np.unique(rng.choice(bt.n_par, min(n_picks, bt.n_par), replace=False))
+    sn_of = np.searchsorted(bt.par_off, picks, side="right") - 1
+    sub = W.subset(bt, sn_of)
+    sub.par_off = np.arange(len(picks) + 1, dtype=np.int64)
+    for k in ("t0", "z", "x0", "x1", "c"):
+        setattr(sub, k, getattr(bt, k)[picks].copy())
+    with torch.cuda.stream(stream):
+        x2, g = s.chi2_grad(db)
+        bf = s.bandflux(db)
+    torch.cuda.synchronize()
+    off = oracle.Oracle.bandflux_offsets(bt)
+    idx = np.concatenate([np.arange(off[sn] + (p - bt.par_off[sn]) * (bt.obs_off[sn + 1] - bt.obs_off[sn]),
+                                    off[sn] + (p - bt.par_off[sn] + 1) * (bt.obs_off[sn + 1] - bt.obs_off[sn]))
+                          for p, sn in zip(picks, sn_of)])
+    pk = torch.as_tensor(picks, device=x2.device)
+    gpu = (x2[pk].cpu().numpy(), g[pk].cpu().numpy(), bf[torch.as_tensor(idx, device=bf.device)].cpu().numpy())
+    del bf
+    o = oracle.Oracle(wl.model, wl.bands)
+    t0 = time.perf_counter()
+    rx2, rg = o.chi2(sub, grad=True)
+    t = time.perf_counter() - t0
+    return {"value": sub.n_bandflux() / t, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+            "sample": f"{len(picks)} seeded (supernova, sample) pairs, one sample each, chi2+grad, "
+                      f"FP64 C with OpenMP ({t:.2f} s)",
+            "error_vs_oracle": error_vs_oracle(sub, gpu, (rx2, rg, o.bandflux(sub)))}
+
+
 def secondary(args, salt_mod, torch, dev, stream):
     """Shorter measurements of the other workloads (not the bench line)."""
     from paper_2504_08081_b300.torch_api import Salt
@@ -371,10 +406,12 @@ def secondary(args, salt_mod, torch, dev, stream):
         ms = statistics.median(durs)
         nbf = wl.batch.n_bandflux()
         flops = algorithmic_flops(wl, grad=True, max_par=20000)
-        out[W.CONFIG_NAMES[cfg]] = {"ms_per_step": ms, "bandfluxes_per_s": nbf / (ms / 1e3),
-                                    "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3),
-                                    "bandfluxes": nbf, "samples": wl.batch.n_par,
-                                    "achieved_tflops": flops / (ms / 1e3) / 1e12}
+        res = {"ms_per_step": ms, "bandfluxes_per_s": nbf / (ms / 1e3),
+               "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3),
+               "bandfluxes": nbf, "samples": wl.batch.n_par,
+               "achieved_tflops": flops / (ms / 1e3) / 1e12}
+        res["cpu_baseline"] = sampled_oracle(wl, s, db, stream, n_picks=128)
+        out[W.CONFIG_NAMES[cfg]] = res
         s.close()
         del db
     from paper_2504_08081_b300 import serving as SV
@@ -648,10 +685,17 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / fp32_peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": KERNEL_NAMES[fam].format(tile),
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                "flop_per_launch": flops}
+                "flop_per_launch": flops,
+                "ncu_counters": measured_counters(kname, W.CONFIG_NAMES[args.workload])}
 
-    # ---- CPU baseline: the oracle as it stands, on the host cores
-    cpu = cpu_baseline(wl, args.cpu_seconds)
+    # ---- CPU baseline: the oracle as it stands, on the host cores, and the
+    # error of this step's results (and of a bandflux call) against its results
+    with torch.cuda.stream(stream):
+        bf_gpu = salt.bandflux(db)
+    torch.cuda.synchronize()
+    cpu = cpu_baseline(wl, args.cpu_seconds,
+                       gpu=(chi2.cpu().numpy(), grad.cpu().numpy(), bf_gpu.cpu().numpy()))
+    del bf_gpu
 
     extras = {}
     if world == 1 and not args.no_extras:
@@ -717,7 +761,20 @@ def measured_traffic(kernel, workload):
     return rec["dram_read_bytes"] + rec["dram_write_bytes"], rec["summary"]
 
 
-def cpu_baseline(wl, budget_s):
+def measured_counters(kernel, workload):
+    """The ncu counters (issue, FMA pipe, L2/L1 throughput, ...) of the same
+    committed capture, under the same source check as measured_traffic."""
+    traffic, src = measured_traffic(kernel, workload)
+    if traffic is None:
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
+    return json.load(open(path)).get(kernel, {}).get("counters")
+
+
+def cpu_baseline(wl, budget_s, gpu=None):
+    """The oracle timed on the host cores over whole passes of the batch; with
+    `gpu` = (chi2, grad, bandflux) of this library on the same batch (numpy),
+    also the error of those results against the oracle's."""
     import oracle
     o = oracle.Oracle(wl.model, wl.bands)
     bt = wl.batch
@@ -725,15 +782,44 @@ def cpu_baseline(wl, budget_s):
     # whole batch passes until the budget is spent (at least one)
     while True:
         t0 = time.perf_counter()
-        o.chi2(bt, grad=True)
+        ref_x2, ref_g = o.chi2(bt, grad=True)
         t += time.perf_counter() - t0
         done += 1
         n_bf += bt.n_bandflux()
         if t >= budget_s or done >= 50:
             break
-    return {"value": n_bf / t, "unit": UNIT, "cores": o.threads, "kind": "oracle",
-            "sample": f"{done} full pass(es) of the {bt.n_sn}-supernova batch, chi2+grad, "
-                      f"FP64 C with OpenMP ({t:.1f} s)"}
+    out = {"value": n_bf / t, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+           "sample": f"{done} full pass(es) of the {bt.n_sn}-supernova batch, chi2+grad, "
+                     f"FP64 C with OpenMP ({t:.1f} s)"}
+    if gpu is not None:
+        out["error_vs_oracle"] = error_vs_oracle(bt, gpu, (ref_x2, ref_g, o.bandflux(bt)))
+    return out
+
+
+def error_vs_oracle(bt, gpu, ref):
+    """Worst errors of (chi2, grad, bandflux) against the FP64 oracle's, in the
+    parity tests' measures: bandflux |dB| / max(|B|, 1e-3 max |B| of its
+    supernova) (limit 1e-5); chi2 |dchi2| / chi2; gradient per sample
+    |d(g s)|_inf / |g s|_inf with s = (0.01, 1 d, |x0|, 1, 0.1) (limit 1e-3)."""
+    import oracle
+    x2, g, bf = gpu
+    rx2, rg, rbf = ref
+    off = oracle.Oracle.bandflux_offsets(bt)
+    scale = np.abs(rbf)
+    for sn in range(bt.n_sn):
+        lo, hi = off[sn], off[sn + 1]
+        if hi > lo:
+            scale[lo:hi] = np.maximum(scale[lo:hi], 1e-3 * np.abs(rbf[lo:hi]).max())
+    bf_err = np.abs(bf.astype(np.float64) - rbf) / np.maximum(scale, 1e-300)
+    x2_err = np.abs(x2 - rx2) / np.maximum(np.abs(rx2), 1e-300)
+    sc = np.stack([np.full(bt.n_par, 0.01), np.ones(bt.n_par), np.abs(bt.x0.astype(np.float64)),
+                   np.ones(bt.n_par), np.full(bt.n_par, 0.1)], 1)
+    gs, rgs = g.astype(np.float64) * sc, rg * sc
+    g_err = np.abs(gs - rgs).max(1) / np.maximum(np.abs(rgs).max(1), 1e-300)
+    return {"bandflux_max_rel": float(bf_err.max()), "chi2_max_rel": float(x2_err.max()),
+            "chi2_median_rel": float(np.median(x2_err)), "grad_max_scaled": float(g_err.max()),
+            "bandfluxes_compared": int(bf.size), "samples_compared": int(x2.size),
+            "limits": {"bandflux": 1e-5, "grad": 1e-3}}
 
 
 def main():

@@ -70,6 +70,47 @@ __device__ __forceinline__ float warp_sum8_scatter(const float (&v)[8], int lane
     return k1;
 }
 
+// L2 prefetch of everything a launch reads (inputs, work list, grid, band
+// tables), cut into 32 KB pieces dealt round-robin over the CTAs; one thread per
+// CTA issues its pieces. Skipped when the total would take a large share of L2.
+__device__ __forceinline__ void prefetch_launch_l2(const ModelParams &m, const BatchDev &b,
+                                                   const WorkItem *items, int n_items) {
+    const void *ptr[14];
+    size_t len[14];
+    int n = 0;
+    auto add = [&](const void *p, size_t l) {
+        if (p && l) { ptr[n] = p; len[n] = l; ++n; }
+    };
+    add(b.mjd, 8 * (size_t)b.n_obs);
+    add(b.band, 4 * (size_t)b.n_obs);
+    add(b.flux, 4 * (size_t)b.n_obs);
+    add(b.fluxerr, 4 * (size_t)b.n_obs);
+    add(b.zp, 4 * (size_t)b.n_obs);
+    add(b.t0, 8 * (size_t)b.n_par);
+    add(b.z, 4 * (size_t)b.n_par);
+    add(b.x0, 4 * (size_t)b.n_par);
+    add(b.x1, 4 * (size_t)b.n_par);
+    add(b.c, 4 * (size_t)b.n_par);
+    add(items, sizeof(WorkItem) * (size_t)n_items);
+    add(m.g01, sizeof(float2) * (size_t)m.n_phase * m.nw_pitch);
+    add(m.band_lam, 4 * (size_t)m.bands.k_total);
+    add(m.band_w, 4 * (size_t)m.bands.k_total);
+    size_t total = 0;
+    for (int r = 0; r < n; ++r) total += len[r];
+    if (total > ((size_t)48 << 20)) return;
+    constexpr size_t PIECE = 32768;
+    const size_t G = gridDim.x, bid = blockIdx.x;
+    size_t base = 0;  // global index of the range's first piece
+    for (int r = 0; r < n; ++r) {
+        const size_t np = (len[r] + PIECE - 1) / PIECE;
+        for (size_t p = base + (bid + G - base % G) % G; p < base + np; p += G) {
+            const size_t off = (p - base) * PIECE;
+            prefetch_l2((const char *)ptr[r] + off, min(PIECE, len[r] - off));
+        }
+        base += np;
+    }
+}
+
 template <int TS, int MODE>
 __global__ void __launch_bounds__(THREADS, 3)
 k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items, int *counter,
@@ -92,6 +133,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *D = (float *)wb;                                    wb += al16(4 * (size_t)NPHW * TS * ND);
     int *rowl = (int *)wb;
 
+    if (tid == 0) prefetch_launch_l2(m, b, items, n_items);
     // with n_items_dev the list's length is read on the device (at most n_items)
     const int n_units = (n_items_dev ? min(*n_items_dev, n_items) : n_items) * NB;
     for (;;) {
@@ -424,6 +466,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             }
         }
         int last = 0;
+        __syncwarp();  // every lane's partial stores precede lane 0's fence
         if (lane == 0) {
             __threadfence();
             last = atomicAdd(scr.arrive + item, 1) == NB - 1;
