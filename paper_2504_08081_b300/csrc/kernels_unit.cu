@@ -219,7 +219,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             int nb_obs = 0;
             // band ids and errors of the next PRE chunks of 32, loaded together so
             // that their latencies overlap
-            constexpr int PRE = 8;
+            constexpr int PRE = 4;
             int pb[PRE];
             float pe[PRE];
             const int base0 = scan;
@@ -259,10 +259,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                 if (mine && rank < room) {
                     const int slot = nb_obs + rank;
                     oIdx[slot] = i;
-                    oMjd[slot] = b.mjd[ob0 + i];
-                    oFlux[slot] = b.flux[ob0 + i];
                     oSig[slot] = e;
-                    oZpf[slot] = zp_scale(b.zp[ob0 + i]);
                 }
                 if (cnt <= room) {
                     nb_obs += cnt;
@@ -277,6 +274,14 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             bad_obs = __any_sync(0xffffffffu, bad_obs);
             __syncwarp();
             if (nb_obs == 0) continue;
+            // the rest of the pass's observations, loaded together (independent loads)
+            for (int q = lane; q < nb_obs; q += 32) {
+                const int64_t gi = ob0 + oIdx[q];
+                oMjd[q] = b.mjd[gi];
+                oFlux[q] = b.flux[gi];
+                oZpf[q] = zp_scale(b.zp[gi]);
+            }
+            __syncwarp();
 
             // touched phase rows of this pass, compacted into rowl
             unsigned msk[NPHW / 32] = {0u, 0u, 0u, 0u};
