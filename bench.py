@@ -414,6 +414,25 @@ def secondary(args, salt_mod, torch, dev, stream):
         out[W.CONFIG_NAMES[cfg]] = res
         s.close()
         del db
+    # the bench workload's shape at 10x the supernovae: how the one-sample
+    # kernel's throughput grows once each warp has many units to run
+    wl = W.config2(seed=1002, n_sn=10000)
+    W.template_flux(wl.batch, np.random.default_rng(1003))
+    s = Salt(wl.model, wl.bands, device=dev.index or 0)
+    with torch.cuda.stream(stream):
+        db = s.upload(wl.batch)
+        torch.cuda.synchronize()
+        durs = time_steps_graph(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_) or \
+            time_steps(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_)
+    ms = statistics.median(durs)
+    fam, tile = s.last_kernel()
+    flops = algorithmic_flops(wl, grad=True)
+    out["batched_chi2_10000sn"] = {"ms_per_step": ms, "bandfluxes_per_s": wl.batch.n_bandflux() / (ms / 1e3),
+                                   "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3),
+                                   "kernel": KERNEL_NAMES[fam].format(tile),
+                                   "achieved_tflops": flops / (ms / 1e3) / 1e12}
+    s.close()
+    del db
     from paper_2504_08081_b300 import serving as SV
     out[W.CONFIG_NAMES[4]] = SV.run_serving_bench(dev.index or 0)
     out["fit_" + W.CONFIG_NAMES[2]] = fit_secondary(dev, args.cpu_seconds)

@@ -18,7 +18,7 @@ namespace uk {
 
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
-constexpr int OBS_W = 128;  // observations of the unit's band cached per pass
+constexpr int OBS_W = 64;   // observations of the unit's band cached per pass
 constexpr int WMAXW = 160;  // window columns per chunk
 constexpr int NPHW = 128;   // phase nodes supported by this kernel
 constexpr int NSLOT = 8;    // doubles per (sample, band) partial: chi2, g[6], invalid flag
@@ -26,18 +26,21 @@ constexpr int NSLOT = 8;    // doubles per (sample, band) partial: chi2, g[6], i
 using fk::al16;
 
 struct Lay {
-    // No block-level staging: the band tables are read through L1, which keeps
-    // the per-block footprint at three resident blocks per SM.
+    // No block-level staging: the band tables are read through L1. With the D
+    // rows sized by the model's phase nodes a block takes ~48 KB (71 nodes, one
+    // sample, gradient); registers hold the kernel at three blocks per SM, and
+    // the rest of the SM's 256 KB of L1/shared memory serves as L1 for the grid.
     size_t warp0, warp_bytes, total;
-    __host__ __device__ Lay(int ts, bool grad) {
+    __host__ __device__ Lay(int ts, bool grad, int np) {
         const int ne = grad ? 3 : 1;
         size_t o = 0;
         warp0 = o;
         // per warp: obs cache (index, mjd, flux, sig, zpf), column responses
-        // [WMAXW][ts][E (, E_c, E_z, pad)], row dots D [NPHW][ts][2 ne], row list [NPHW]
+        // [WMAXW][ts][E (, E_c, E_z, pad)], row dots D [np][ts][2 ne], row list [np]
+        // (np = the model's phase nodes, at most NPHW)
         warp_bytes = al16(4 * OBS_W) + al16(8 * OBS_W) + 3 * al16(4 * OBS_W) +
-                     al16(4 * (size_t)WMAXW * ts * (grad ? 4 : 1)) + al16(4 * (size_t)NPHW * ts * 2 * ne) +
-                     al16(4 * NPHW);
+                     al16(4 * (size_t)WMAXW * ts * (grad ? 4 : 1)) + al16(4 * (size_t)np * ts * 2 * ne) +
+                     al16(4 * (size_t)np);
         o += WARPS * warp_bytes;
         total = o;
     }
@@ -120,7 +123,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     constexpr int ND = 2 * NE;        // row dots per (row, sample): x surfaces M0, M1
     constexpr int NEP = GRAD ? 4 : 1; // column-response slots per (column, sample)
     extern __shared__ __align__(16) unsigned char smem[];
-    const Lay L(TS, GRAD);
+    const Lay L(TS, GRAD, m.n_phase);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int NB = m.bands.n_bands, NW = m.n_wave, NP = m.n_phase;
     unsigned char *wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
@@ -130,7 +133,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *oSig = (float *)wb;                                 wb += al16(4 * OBS_W);
     float *oZpf = (float *)wb;                                 wb += al16(4 * OBS_W);
     float *E = (float *)wb;                                    wb += al16(4 * (size_t)WMAXW * TS * NEP);
-    float *D = (float *)wb;                                    wb += al16(4 * (size_t)NPHW * TS * ND);
+    float *D = (float *)wb;                                    wb += al16(4 * (size_t)NP * TS * ND);
     int *rowl = (int *)wb;
 
     if (tid == 0) prefetch_launch_l2(m, b, items, n_items);
@@ -518,7 +521,7 @@ template <int TS, int MODE>
 static cudaError_t launch_uk(const salt_ctx *ctx, const WorkItem *items_d, int n_items, int *counter_d,
                              void *scratch, const BatchDev &b, const OutDev &o, cudaStream_t st,
                              const int *n_items_dev) {
-    const size_t smem = uk::Lay(TS, MODE == MODE_GRAD).total;
+    const size_t smem = uk::Lay(TS, MODE == MODE_GRAD, ctx->mp.n_phase).total;
     static std::atomic<int> attr_done[64];
     cudaError_t e;
     const int dv = ctx->device & 63;
