@@ -213,7 +213,9 @@ typedef enum {
                                   (CTA family; the warp families take 1 or 2) or 0 = default */
     SALT_OPT_GRAPHS = 3,       /* 1 (default) = a plan call repeated with the same batch and output
                                   pointers, mode and kernel is captured into a CUDA graph once and
-                                  replayed on later such calls; 0 = always launch directly */
+                                  replayed on later such calls (up to four pointer sets per plan,
+                                  mode and kernel are remembered, so alternating buffers replay
+                                  too); 0 = always launch directly */
     SALT_OPT_SERVE_CHUNK = 4,  /* serving: samples per work item (default 8; larger chunks
                                   cut per-item overhead but lengthen each item's latency) */
     SALT_OPT_LAST_KERNEL = 5   /* read-only: SALT_KERNEL_* x 32 + samples per tile of the kernel
