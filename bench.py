@@ -699,13 +699,23 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the max SM clock
     achieved = flops / (ms / 1e3) / 1e12
     kname = KERNEL_NAMES[fam].format(tile)
+    # the derived FP32 peak checked by the library's FMA microbenchmark (and the
+    # L2 / shared-memory read bandwidths), measured after the timed region
+    try:
+        pk = salt.measure_peaks()
+        peak_check = {"fp32_tflops_measured": pk["fp32_tflops"], "fp32_tflops_derived": sm_count * 128 * 2 *
+                      max_mhz * 1e6 / 1e12, "l2_read_gbs": pk["l2_read_gbs"],
+                      "smem_read_gbs": pk["smem_read_gbs"], "source": "salt_measure_peaks"}
+    except Exception as ex:  # a diagnostic must not sink the bench line
+        peak_check = {"error": repr(ex)}
     traffic, traffic_src = measured_traffic(kname, W.CONFIG_NAMES[args.workload])
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": KERNEL_NAMES[fam].format(tile),
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "flop_per_launch": flops,
-                "ncu_counters": measured_counters(kname, W.CONFIG_NAMES[args.workload])}
+                "ncu_counters": measured_counters(kname, W.CONFIG_NAMES[args.workload]),
+                "peak_check": peak_check}
 
     # ---- CPU baseline: the oracle as it stands, on the host cores, and the
     # error of this step's results (and of a bandflux call) against its results

@@ -401,6 +401,27 @@ int salt_nested(salt_ctx *ctx, const salt_batch *batch, const double *lower, con
 int salt_chi2_grad_noalloc(salt_ctx *ctx, const salt_batch *batch, double *chi2, float *grad,
                            void *cuda_stream);
 
+/* ------------------------------------------------- device peaks ---------- */
+
+/* Microbenchmarks of the context's device (the paper has no counterpart: they
+ * are the measured side of the roofline the photometry kernels are reported
+ * against). */
+typedef struct {
+    double fp32_tflops;      /* FMA throughput, 2 FLOP per FMA: 8 independent FMA chains per
+                                thread, 8 blocks of 256 threads per SM, best of 3 launches */
+    double l2_read_gbs;      /* 200 passes of 16-byte L2-only loads (ld.global.cg) over a 32 MiB
+                                buffer (L2-resident) */
+    double smem_read_gbs;    /* conflict-free 16-byte shared-memory loads, all SMs */
+    double sm_clock_max_mhz; /* the device's maximum SM clock (cudaDevAttrClockRate) */
+    int32_t num_sms;
+} salt_peaks;
+
+/* Runs the three microbenchmarks on a private stream (synchronous, ~50 ms;
+ * allocates and frees 32 MiB plus a small sink) and fills *out.
+ * SALT_ERR_INVALID for NULL arguments, SALT_ERR_OOM / SALT_ERR_CUDA with
+ * salt_last_error set otherwise. */
+int salt_measure_peaks(salt_ctx *ctx, salt_peaks *out);
+
 /* ---------------------------------------------------------------- misc ---- */
 
 const char *salt_status_str(int status);

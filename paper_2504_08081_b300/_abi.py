@@ -43,6 +43,7 @@ EXPORTS = [
     "salt_set_option", "salt_get_option", "salt_serve_submit", "salt_serve_poll",
     "salt_serve_cancel", "salt_serve_stats_get", "salt_status_str", "salt_last_error",
     "salt_chi2_grad_noalloc", "salt_fit", "salt_register_band", "salt_band_load", "salt_nested",
+    "salt_measure_peaks",
 ]
 
 # Fitting (salt_fit): parameter bits, outcome codes.
@@ -107,6 +108,11 @@ class ServeStats(C.Structure):
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("l2_read_gbs", C.c_double), ("smem_read_gbs", C.c_double),
+                ("sm_clock_max_mhz", C.c_double), ("num_sms", C.c_int32)]
+
+
 _lib = None
 
 
@@ -136,6 +142,7 @@ def lib():
     L.salt_nested.argtypes = [p, C.POINTER(BatchDesc), p, p, C.POINTER(NestedOpts), p, p, p, p, p, p]
     L.salt_register_band.argtypes = [p, C.POINTER(BandDesc), C.POINTER(i32)]
     L.salt_band_load.argtypes = [p, C.c_char_p, C.c_double, C.c_double, p, p, i32, C.POINTER(i32)]
+    L.salt_measure_peaks.argtypes = [p, C.POINTER(Peaks)]
     L.salt_check.argtypes = [p, p]
     L.salt_set_option.argtypes = [p, i32, i64]
     L.salt_get_option.argtypes = [p, i32, C.POINTER(i64)]

@@ -204,6 +204,13 @@ class Salt:
         v = self.ctx.get_option(_abi.SALT_OPT_LAST_KERNEL)
         return v // 32, v % 32
 
+    def measure_peaks(self) -> dict:
+        """FP32 FMA rate, L2 and shared-memory read bandwidth of this device
+        (salt_measure_peaks microbenchmarks; synchronous)."""
+        pk = _abi.Peaks()
+        self.ctx.check(_abi.lib().salt_measure_peaks(self.ctx.h, C.byref(pk)))
+        return {f: getattr(pk, f) for f, _ in _abi.Peaks._fields_}
+
     # -- serving -------------------------------------------------------------
     def submit(self, n_obs, mjd, band, flux, fluxerr, zp, t0, z, x0, x1, c, want_grad) -> int:
         arrs = [np.ascontiguousarray(mjd, np.float64), np.ascontiguousarray(band, np.int32),
