@@ -81,6 +81,13 @@ def algorithmic_flops(wl, grad=True, max_par=2_000_000):
     """Exact count of the factorised method's necessary FP32 work for one
     pass over the batch: per (sample, band) the in-grid band samples, the
     window columns and the distinct phase rows its own observations touch."""
+    return algorithmic_work(wl, grad, max_par)[0]
+
+
+def algorithmic_work(wl, grad=True, max_par=2_000_000):
+    """(FLOP, grid bytes) of one pass: the FP32 work above, and the grid
+    values the row dots read, touched rows x window columns x 8 bytes (M0 and
+    M1 as one float2) per (sample, band)."""
     m, bt = wl.model, wl.batch
     nb = len(wl.bands)
     lam_lo = np.array([b.wave[0] for b in wl.bands])
@@ -89,6 +96,7 @@ def algorithmic_flops(wl, grad=True, max_par=2_000_000):
     n_obs = np.diff(bt.obs_off)
     n_par = np.diff(bt.par_off)
     total = 0.0
+    grid_bytes = 0.0
     rng = np.random.default_rng(0)
     # subsample very large batches and scale (the count is a sum over samples)
     idx_all = np.arange(bt.n_par)
@@ -124,13 +132,14 @@ def algorithmic_flops(wl, grad=True, max_par=2_000_000):
                     cols = f0[1] + 3 - f0[0] + 1
                 else:
                     cols = 0
+                grid_bytes += 8.0 * rows * cols
                 if grad:
                     total += (FLOP_K_GRAD * kin + FLOP_RC_GRAD * rows * cols + FLOP_C_GRAD * cols
                               + FLOP_OBS_GRAD * nb_obs)
                 else:
                     total += FLOP_K_FWD * kin + FLOP_RC_FWD * rows * cols + FLOP_OBS_FWD * nb_obs
     del lam_lo, lam_hi, nb
-    return total * scale
+    return total * scale, grid_bytes * scale
 
 
 class ClockSampler:
@@ -690,7 +699,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (the one the plan launched)
     fam, tile = salt.last_kernel()
-    flops = algorithmic_flops(wl, grad=True)
+    flops, grid_bytes = algorithmic_work(wl, grad=True)
     clocks = clk.summary()
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -716,6 +725,14 @@ def run_ours(args, rank, world, local_rank):
                 "flop_per_launch": flops,
                 "ncu_counters": measured_counters(kname, W.CONFIG_NAMES[args.workload]),
                 "peak_check": peak_check}
+    # the same launch against the measured L2 read bandwidth: the grid values
+    # the row dots must read (the kernel's on-chip gather)
+    l2_peak = peak_check.get("l2_read_gbs")
+    l2_achieved = grid_bytes / (ms / 1e3) / 1e9
+    roofline_l2 = {"bound": "l2", "achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s",
+                   "frac": l2_achieved / l2_peak if l2_peak else None, "bytes_per_launch": grid_bytes,
+                   "bytes": "grid values read by the row dots: touched rows x window columns x 8 B "
+                            "per (sample, band)", "peak_source": "salt_measure_peaks (measured)"}
 
     # ---- CPU baseline: the oracle as it stands, on the host cores, and the
     # error of this step's results (and of a bandflux call) against its results
@@ -759,6 +776,7 @@ def run_ours(args, rank, world, local_rank):
                 "serial_ms_per_step": e2e_serial_ms,
                 "serial_value": bt.n_bandflux() / (e2e_serial_ms / 1e3)},
         "roofline": roofline,
+        "roofline_l2": roofline_l2,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
