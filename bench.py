@@ -38,13 +38,17 @@ METRIC = "bandfluxes/s and chi2+grad evals/s on 1 B300 vs oracle; serving p50/p9
 UNIT = "bandfluxes/s"
 
 # Algorithmic FP32 work of the factorised method (FLOP per unit; each FMA = 2).
+# The gradient is counted in its cheapest form (no value computed twice): the
+# column responses E, E_c = dE/dc and E_z (the lambda' part of dE/dz) built in
+# one pass, forward row dots of E, the adjoint rows back-projected once
+# (Q = Y^T H), and dchi2/dc, dchi2/dz as the dots Q.E_c, Q.E_z.
 FLOP_K_FWD = 33      # per (sample, band, in-grid band sample), forward: lambda', Keys weights,
                      # colour law, exp2, weight, 4 weighted taps and their column sums
-FLOP_K_GRAD = 88     # ... plus the adjoint: Keys weights and derivatives, colour law and slope,
-                     # exp2, the 8-term dot with the back-projected adjoint, dchi2/dc and dchi2/dz
+FLOP_K_GRAD = 74     # ... with Keys derivatives, colour-law slope, 12 weighted taps (E, E_c,
+                     # E_z) and their column sums
 FLOP_RC_GRAD = 8     # per (sample, band, touched row, window column): forward + reverse FMA pair
 FLOP_RC_FWD = 4
-FLOP_C_GRAD = 2      # per (sample, band, window column): Q = Q0 + x1 Q1
+FLOP_C_GRAD = 4      # per (sample, band, window column): Q.E_c and Q.E_z
 FLOP_OBS_GRAD = 60   # per (sample, observation): phase taps, 4-row combine, residual, gradient
 FLOP_OBS_FWD = 24
 
