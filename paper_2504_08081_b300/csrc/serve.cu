@@ -14,7 +14,11 @@
 // requests wait to be grouped into larger ones. A tick's admitted requests are
 // packed into a pinned staging buffer and uploaded with one copy per array and
 // one scatter kernel. Uploads, kernels and downloads run on three streams
-// ordered by events, so copies overlap other requests' kernels. A request's
+// ordered by events, so copies overlap other requests' kernels. A submission
+// wakes the scheduler only when it is idle; while work is queued or in
+// flight the scheduler comes back every ~20 us by itself, so a burst of
+// submissions neither waits on a scheduler pass per request nor splits into
+// one launch per request. A request's
 // chunks go through exactly the same per-item code whatever else shares the
 // launch, so its results are bitwise identical alone and in a mix.
 #include <algorithm>
@@ -184,6 +188,7 @@ struct ServeEngine {
     uint64_t next_ticket = 1;
     uint64_t n_submitted = 0, n_completed = 0, n_cancelled = 0, n_rejected = 0, n_launches = 0;
     bool stop = false;
+    bool idle = false;  // the engine thread waits for work with nothing queued or in flight
     std::string fatal;
     std::thread th;
 
@@ -491,10 +496,14 @@ void run(ServeEngine *e) {
             break;
         }
         if (!has_work(e)) {
+            e->idle = true;
             e->cv_work.wait(lk);
+            e->idle = false;
             continue;
         }
         tick(e);
+        // with work queued or in flight the engine comes back on its own after a
+        // short wait; submissions meanwhile only queue (they wake an idle engine)
         if (has_work(e)) e->cv_work.wait_for(lk, std::chrono::microseconds(20));
     }
 }
@@ -617,6 +626,7 @@ int serve_submit(ServeEngine *e, const salt_request *q, uint64_t *ticket) {
     r->x1.assign(q->x1, q->x1 + S);
     r->c.assign(q->c, q->c + S);
     r->t_submit = now_ms();
+    bool wake = false;
     {
         std::lock_guard<std::mutex> lk(e->mu);
         if (!e->fatal.empty()) return SALT_ERR_CUDA;
@@ -626,8 +636,9 @@ int serve_submit(ServeEngine *e, const salt_request *q, uint64_t *ticket) {
         e->queue.push_back(r->ticket);
         e->reqs.emplace(r->ticket, std::move(r));
         e->n_submitted++;
+        wake = e->idle;
     }
-    e->cv_work.notify_one();
+    if (wake) e->cv_work.notify_one();
     return SALT_OK;
 }
 
