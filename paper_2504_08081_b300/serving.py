@@ -150,6 +150,31 @@ def run_serving_bench(device: int = 0, n_req: int = 20000, seed: int = 1004,
                                      "requests": n, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                                      "launches": st["launches"]}
         s.close()
+    # the same requests as two batch calls (the chi^2-only ones, the gradient
+    # ones): the device time the stream needs without any serving machinery
+    import torch
+    s = Salt(wl.model, wl.bands, device=device)
+    g_idx = [i for i, r in enumerate(reqs) if r.want_grad]
+    c_idx = [i for i, r in enumerate(reqs) if not r.want_grad]
+    dbg = s.upload(W.subset(wl.batch, g_idx))
+    dbc = s.upload(W.subset(wl.batch, c_idx))
+    for _ in range(2):  # tune and warm
+        s.chi2_grad(dbg)
+        s.chi2(dbc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.chi2_grad(dbg)
+    s.chi2(dbc)
+    e1.record()
+    e1.synchronize()
+    gpu_s = e0.elapsed_time(e1) / 1e3
+    out["batch_equivalent"] = {"device_s": gpu_s, "req_per_s": len(reqs) / gpu_s,
+                               "bandfluxes_per_s": out["bandfluxes_total"] / gpu_s,
+                               "how": "the whole stream as two batch calls (chi^2 only, chi^2 + gradient)"}
+    out["saturated_vs_batch"] = sat / (len(reqs) / gpu_s)
+    del dbg, dbc
+    s.close()
     # plain per-request launches on the same stream (closed loop, bounded time)
     s = Salt(wl.model, wl.bands, device=device)
     k, wall, lat = plain_per_request(s, reqs, limit_s=max_replay_s)
