@@ -88,6 +88,14 @@ def algorithmic_flops(wl, grad=True, max_par=2_000_000):
     return algorithmic_work(wl, grad, max_par)[0]
 
 
+def interval(x, x0, dx, nodes):
+    """Interval index of x on a model axis: uniform (x0, dx) or, with nodes, the
+    last node at or below x."""
+    if nodes is None:
+        return np.floor((np.asarray(x) - x0) / dx).astype(np.int64)
+    return np.searchsorted(np.asarray(nodes), np.asarray(x), side="right").astype(np.int64) - 1
+
+
 def algorithmic_work(wl, grad=True, max_par=2_000_000):
     """(FLOP, grid bytes) of one pass: the FP32 work above, and the grid
     values the row dots read, touched rows x window columns x 8 bytes (M0 and
@@ -119,7 +127,7 @@ def algorithmic_work(wl, grad=True, max_par=2_000_000):
             p = (bt.mjd[lo:hi] - bt.t0[j]) * a
             bands = bt.band[lo:hi]
             ok = (p >= m.phase0) & (p <= m.phase_max)
-            iv = np.clip(np.floor((p - m.phase0) / m.dphase).astype(np.int64), 0, m.n_phase - 2)
+            iv = np.clip(interval(p, m.phase0, m.dphase, m.phase_nodes), 0, m.n_phase - 2)
             first = np.where(iv == 0, 0, np.where(iv == m.n_phase - 2, m.n_phase - 4, iv - 1))
             for b in np.unique(bands):
                 sel = (bands == b)
@@ -130,8 +138,7 @@ def algorithmic_work(wl, grad=True, max_par=2_000_000):
                 kin = int(((lr >= m.wave0) & (lr <= m.wave_max)).sum())
                 if kin:
                     lri = lr[(lr >= m.wave0) & (lr <= m.wave_max)]
-                    c0 = np.clip(np.floor((lri[[0, -1]] - m.wave0) / m.dwave).astype(np.int64), 0,
-                                 m.n_wave - 2)
+                    c0 = np.clip(interval(lri[[0, -1]], m.wave0, m.dwave, m.wave_nodes), 0, m.n_wave - 2)
                     f0 = [0 if c == 0 else (m.n_wave - 4 if c == m.n_wave - 2 else c - 1) for c in c0]
                     cols = f0[1] + 3 - f0[0] + 1
                 else:
@@ -446,6 +453,26 @@ def secondary(args, salt_mod, torch, dev, stream):
                                    "achieved_tflops": flops / (ms / 1e3) / 1e12}
     s.close()
     del db
+    # non-uniform (SALT3-NIR-shaped) grid: 66 x 991 nodes, binary-search indexing
+    wl = W.config_nir(n_sn=4000, n_samples=4)
+    W.template_flux(wl.batch, np.random.default_rng(1007))
+    s = Salt(wl.model, wl.bands, device=dev.index or 0)
+    with torch.cuda.stream(stream):
+        db = s.upload(wl.batch)
+        torch.cuda.synchronize()
+        durs = time_steps_graph(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_) or \
+            time_steps(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_)
+    ms = statistics.median(durs)
+    fam, tile = s.last_kernel()
+    flops = algorithmic_flops(wl, grad=True)
+    out["nir_nonuniform_4000sn_x4"] = {
+        "ms_per_step": ms, "bandfluxes_per_s": wl.batch.n_bandflux() / (ms / 1e3),
+        "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3), "kernel": KERNEL_NAMES[fam].format(tile),
+        "achieved_tflops": flops / (ms / 1e3) / 1e12, "grid": [wl.model.n_phase, wl.model.n_wave],
+        "cpu_baseline": sampled_oracle(wl, s, db, stream, n_picks=128)}
+    s.close()
+    del db
+    out["band_files"] = band_file_secondary(dev)
     from paper_2504_08081_b300 import serving as SV
     out[W.CONFIG_NAMES[4]] = SV.run_serving_bench(dev.index or 0)
     out["fit_" + W.CONFIG_NAMES[2]] = fit_secondary(dev, args.cpu_seconds)
@@ -505,6 +532,38 @@ def nested_secondary(dev, cpu_seconds, n_live=1024, n_batch=256, n_steps=10):
                            "sample": f"supernova 0, {r['iterations']} iterations of the reference sampler "
                                      f"(FP64 oracle chi^2, OpenMP over proposals, {t_cpu:.1f} s)"}
     return out
+
+
+def band_file_secondary(dev):
+    """Bandpass files (salt_band_load) and registration (salt_register_band):
+    a 2001-sample transmission curve in nm, comma separated with a comment
+    header, read and resampled onto 5 A, then added to a live context; wall
+    time of each (host work plus the band-table upload)."""
+    import tempfile
+    from paper_2504_08081_b300 import _abi
+    from paper_2504_08081_b300.torch_api import Salt
+    wl = make_workload(2, 0)
+    s = Salt(wl.model, wl.bands, device=dev.index or 0)
+    lam_nm = np.linspace(400.0, 600.0, 2001)
+    trans = np.exp(-0.5 * ((lam_nm - 500.0) / 30.0) ** 2)
+    with tempfile.NamedTemporaryFile("w", suffix=".dat", delete=False) as f:
+        f.write("# wavelength_nm, transmission\n")
+        for a, t in zip(lam_nm, trans):
+            f.write(f"{a:.4f}, {t:.8f}\n")
+        path = f.name
+    try:
+        t0 = time.perf_counter()
+        for _ in range(20):
+            wave, tr = _abi.load_band(path, wave_scale=10.0, step=5.0)
+        t_load = (time.perf_counter() - t0) / 20
+        t0 = time.perf_counter()
+        idx = s.register_band(wave, tr)
+        t_reg = time.perf_counter() - t0
+    finally:
+        os.unlink(path)
+    s.close()
+    return {"file_samples": len(lam_nm), "resampled_samples": len(wave), "load_ms": 1e3 * t_load,
+            "register_ms": 1e3 * t_reg, "band_index": idx}
 
 
 def fit_secondary(dev, cpu_seconds):
