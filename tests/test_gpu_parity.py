@@ -274,3 +274,38 @@ def test_gradient_against_central_differences_on_gpu(cfg3_sub):
         fd = ((xp - xm) / (up.double() - dn.double())).cpu().numpy()
         scale = np.abs(g[:, q]) + 1e-2 * np.abs(g[:, q]).max() + 1e-300
         assert np.median(np.abs(fd - g[:, q]) / scale) < 1e-2, name
+
+
+def _crowded_workload():
+    """Supernovae whose observations overflow every kernel's per-pass caches:
+    700 observations in one band (several observation passes and chunks),
+    130 split over two bands, and a 1-sample supernova with 200 observations
+    in one band."""
+    rng = np.random.default_rng(91)
+    model = W.make_model(rng)
+    bands = [W.gaussian_band(5000.0, 181), W.gaussian_band(6500.0, 221)]
+    n_obs = [700, 130, 200]
+    n_par = [5, 3, 1]
+    z = [0.08, 0.3, 0.15]
+    bt = W.make_batch(rng, model, bands, n_obs, z, n_par, perturb=W.PERTURB)
+    bt.band[:] = 0
+    lo, hi = bt.obs_off[1], bt.obs_off[2]
+    bt.band[lo:hi] = rng.integers(0, 2, size=hi - lo).astype(np.int32)
+    return W.Workload("crowded", model, bands, bt)
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_observation_passes_overflowing_the_caches(kernel):
+    wl = _crowded_workload()
+    o = H.with_oracle_flux(wl)
+    bt = wl.batch
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(bt)
+    ref_bf = o.bandflux(bt)
+    H.assert_bandflux_close(bt, s.bandflux(db).cpu().numpy(), ref_bf)
+    x2, g = s.chi2_grad(db)
+    ref_x2, ref_g = o.chi2(bt, grad=True)
+    H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    s.check()
