@@ -188,7 +188,8 @@ int salt_bandflux_offsets(int64_t n_sn, const int64_t *obs_off, const int64_t *p
 
 /* Bandflux (Eq. 2, zero-point scaled) of every (sample, observation) pair of
  * every supernova: out[bf_off[s] + j*n_obs(s) + i] for local sample j and
- * local observation i. out: DEVICE float32 [bf_off[n_sn]]. */
+ * local observation i. out: DEVICE float32 [bf_off[n_sn]] (may be NULL when
+ * bf_off[n_sn] = 0). */
 int salt_bandflux(salt_ctx *ctx, const salt_batch *batch, float *out, void *cuda_stream);
 
 /* chi^2 of every parameter sample against its supernova's observations.

@@ -758,7 +758,13 @@ static int batch_call(salt_ctx *ctx, const salt_batch *bt, int mode, float *bf, 
         return set_err(ctx, SALT_ERR_INVALID, "missing observation arrays");
     if (n_par > 0 && (!bt->t0 || !bt->z || !bt->x0 || !bt->x1 || !bt->c))
         return set_err(ctx, SALT_ERR_INVALID, "missing parameter arrays");
-    if (mode == MODE_BANDFLUX && !bf && n_par > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
+    if (mode == MODE_BANDFLUX && !bf) {
+        // an output is needed only when there is a bandflux to write
+        int64_t n_bf = 0;
+        for (int64_t s = 0; s < bt->n_sn && n_bf == 0; ++s)
+            n_bf += (bt->obs_off[s + 1] - bt->obs_off[s]) * (bt->par_off[s + 1] - bt->par_off[s]);
+        if (n_bf > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
+    }
     if (mode != MODE_BANDFLUX && !chi2 && n_par > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
     if (mode == MODE_GRAD && !grad && n_par > 0) return set_err(ctx, SALT_ERR_INVALID, "missing output");
     if (!plan) {

@@ -309,3 +309,35 @@ def test_observation_passes_overflowing_the_caches(kernel):
     H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
     H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
     s.check()
+
+
+def _empty_like(bt, n_obs_per_sn, n_par_per_sn):
+    """A batch with the given per-supernova observation and sample counts,
+    arrays filled from bt's first entries (bt must hold enough of them)."""
+    oo = np.concatenate([[0], np.cumsum(n_obs_per_sn)]).astype(np.int64)
+    po = np.concatenate([[0], np.cumsum(n_par_per_sn)]).astype(np.int64)
+    no, npar = int(oo[-1]), int(po[-1])
+    return W.Batch(obs_off=oo, mjd=bt.mjd[:no].copy(), band=bt.band[:no].copy(), flux=bt.flux[:no].copy(),
+                   fluxerr=bt.fluxerr[:no].copy(), zp=bt.zp[:no].copy(), par_off=po, t0=bt.t0[:npar].copy(),
+                   z=bt.z[:npar].copy(), x0=bt.x0[:npar].copy(), x1=bt.x1[:npar].copy(), c=bt.c[:npar].copy())
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_empty_batches(kernel):
+    """No supernovae; supernovae without samples; supernovae without
+    observations: every call succeeds, with chi^2 = 0 and a zero gradient
+    where there are samples but nothing to compare."""
+    wl = W.config2(n_sn=4)
+    H.with_oracle_flux(wl)
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    for n_obs, n_par in (([], []), ([10, 0, 7], [0, 0, 0]), ([0, 0], [3, 1])):
+        bt = _empty_like(wl.batch, n_obs, n_par)
+        for plan in (True, False):
+            db = s.upload(bt, plan=plan)
+            x2, g = s.chi2_grad(db)
+            bf = s.bandflux(db)
+            x2c = s.chi2(db)
+            assert x2.shape == (bt.n_par,) and g.shape == (bt.n_par, 5) and bf.numel() == 0
+            assert bool((x2 == 0).all()) and bool((g == 0).all()) and bool((x2c == 0).all())
+    s.check()
