@@ -341,3 +341,44 @@ def test_empty_batches(kernel):
             assert x2.shape == (bt.n_par,) and g.shape == (bt.n_par, 5) and bf.numel() == 0
             assert bool((x2 == 0).all()) and bool((g == 0).all()) and bool((x2c == 0).all())
     s.check()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_maximum_grid(kernel):
+    """The largest grid a context takes: 256 phase nodes (0.27 d apart, so an
+    observation season touches ~220 rows) by 2001 wavelength nodes (5 A).
+    The warp kernels (at most 128 phase nodes) refuse it when forced; the
+    autotuner leaves them out."""
+    from paper_2504_08081_b300 import SaltError
+    rng = np.random.default_rng(5)
+    model = W.make_model(rng, wave_max=12000.0, phase=(-20.0, 50.0, 70.0 / 255.0), dwave=5.0)
+    assert model.n_phase == 256 and model.n_wave == 2001
+    bands = [W.gaussian_band(4500.0, 201), W.gaussian_band(6500.0, 281), W.gaussian_band(9000.0, 301)]
+    n_obs = [60, 45, 30, 52]
+    n_par = [3, 9, 1, 4]
+    bt = W.make_batch(rng, model, bands, n_obs, [0.05, 0.3, 0.6, 0.15], n_par, perturb=W.PERTURB)
+    wl = W.Workload("maxgrid", model, bands, bt)
+    o = H.with_oracle_flux(wl)
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(bt)
+    if kernel in ("unit", "bandwarp"):
+        with pytest.raises(SaltError):
+            s.chi2_grad(db)
+        return
+    ref_bf = o.bandflux(bt)
+    H.assert_bandflux_close(bt, s.bandflux(db).cpu().numpy(), ref_bf)
+    x2, g = s.chi2_grad(db)
+    ref_x2, ref_g = o.chi2(bt, grad=True)
+    H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    s.check()
+
+
+def test_grid_beyond_the_maximum_is_refused():
+    from paper_2504_08081_b300 import SaltError
+    rng = np.random.default_rng(6)
+    model = W.make_model(rng, phase=(-20.0, 50.0, 70.0 / 256.0))
+    assert model.n_phase == 257
+    with pytest.raises(SaltError):
+        _salt(W.Workload("toolarge", model, [W.gaussian_band(5000.0, 201)], None))
