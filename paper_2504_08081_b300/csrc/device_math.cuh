@@ -198,62 +198,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 namespace salt {
 
-// ---- Bulk asynchronous copies (TMA engine) into shared memory, completed on an mbarrier.
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// order this thread's earlier generic-proxy shared-memory accesses before
-// later async-proxy (bulk copy) accesses
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// global -> shared bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for phase `parity` of the barrier, giving up after a bounded number of
-// polls (each try_wait itself suspends for a bounded, system-defined time).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 20); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-}  // namespace salt
-
-namespace salt {
-
 // Prefetch [p, p + bytes) into L2 with bulk prefetches (TMA engine); only the
 // 16-byte aligned interior is requested, so nothing outside the range is touched.
 __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
