@@ -900,10 +900,33 @@ def cpu_baseline(wl, budget_s, gpu=None):
             break
     out = {"value": n_bf / t, "unit": UNIT, "cores": o.threads, "kind": "oracle",
            "sample": f"{done} full pass(es) of the {bt.n_sn}-supernova batch, chi2+grad, "
-                     f"FP64 C with OpenMP ({t:.1f} s)"}
+                     f"FP64 C with OpenMP ({t:.1f} s)", "cpu_model": cpu_model()}
+    # the same oracle on one thread, over the first supernovae (about 2 s)
+    o1 = oracle.Oracle(wl.model, wl.bands, threads=1)
+    n1 = min(bt.n_sn, 100)
+    sub = W.subset(bt, np.arange(n1))
+    t0 = time.perf_counter()
+    o1.chi2(sub, grad=True)
+    t1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": sub.n_bandflux() / t1, "unit": UNIT,
+                            "sample": f"first {n1} supernovae, chi2+grad, one thread ({t1:.1f} s)"}
     if gpu is not None:
         out["error_vs_oracle"] = error_vs_oracle(bt, gpu, (ref_x2, ref_g, o.bandflux(bt)))
     return out
+
+
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo) and thread count."""
+    name = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{name} ({os.cpu_count()} threads)"
 
 
 def error_vs_oracle(bt, gpu, ref):
