@@ -412,71 +412,69 @@ def sampled_oracle(wl, s, db, stream, n_picks):
 
 
 def secondary(args, salt_mod, torch, dev, stream):
-    """Shorter measurements of the other workloads (not the bench line)."""
+    """Shorter measurements of the other workloads (not the bench line), each
+    guarded so that one failing record does not drop the others."""
     from paper_2504_08081_b300.torch_api import Salt
     out = {}
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    for cfg in (3, 5):
-        wl = make_workload(cfg, 0)
+
+    def timed_workload(wl, steps, sampled_pairs, max_par=2_000_000):
+        """chi^2 + gradient steps of a workload (graph-timed, L2 flushed), its
+        counted FLOP rate and, optionally, sampled errors against the oracle."""
         s = Salt(wl.model, wl.bands, device=dev.index or 0)
-        with torch.cuda.stream(stream):
-            db = s.upload(wl.batch)
-            torch.cuda.synchronize()
-            durs = time_steps(lambda: s.chi2_grad(db), 5, 2, stream, flush=flush_buf.zero_)
-        ms = statistics.median(durs)
-        nbf = wl.batch.n_bandflux()
-        flops = algorithmic_flops(wl, grad=True, max_par=20000)
-        res = {"ms_per_step": ms, "bandfluxes_per_s": nbf / (ms / 1e3),
-               "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3),
-               "bandfluxes": nbf, "samples": wl.batch.n_par,
-               "achieved_tflops": flops / (ms / 1e3) / 1e12}
-        res["cpu_baseline"] = sampled_oracle(wl, s, db, stream, n_picks=128)
-        out[W.CONFIG_NAMES[cfg]] = res
-        s.close()
-        del db
-    # the bench workload's shape at 10x the supernovae: how the one-sample
-    # kernel's throughput grows once each warp has many units to run
-    wl = W.config2(seed=1002, n_sn=10000)
-    W.template_flux(wl.batch, np.random.default_rng(1003))
-    s = Salt(wl.model, wl.bands, device=dev.index or 0)
-    with torch.cuda.stream(stream):
-        db = s.upload(wl.batch)
-        torch.cuda.synchronize()
-        durs = time_steps_graph(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_) or \
-            time_steps(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_)
-    ms = statistics.median(durs)
-    fam, tile = s.last_kernel()
-    flops = algorithmic_flops(wl, grad=True)
-    out["batched_chi2_10000sn"] = {"ms_per_step": ms, "bandfluxes_per_s": wl.batch.n_bandflux() / (ms / 1e3),
-                                   "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3),
-                                   "kernel": KERNEL_NAMES[fam].format(tile),
-                                   "achieved_tflops": flops / (ms / 1e3) / 1e12}
-    s.close()
-    del db
-    # non-uniform (SALT3-NIR-shaped) grid: 66 x 991 nodes, binary-search indexing
-    wl = W.config_nir(n_sn=4000, n_samples=4)
-    W.template_flux(wl.batch, np.random.default_rng(1007))
-    s = Salt(wl.model, wl.bands, device=dev.index or 0)
-    with torch.cuda.stream(stream):
-        db = s.upload(wl.batch)
-        torch.cuda.synchronize()
-        durs = time_steps_graph(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_) or \
-            time_steps(lambda: s.chi2_grad(db), 10, 3, stream, flush=flush_buf.zero_)
-    ms = statistics.median(durs)
-    fam, tile = s.last_kernel()
-    flops = algorithmic_flops(wl, grad=True)
-    out["nir_nonuniform_4000sn_x4"] = {
-        "ms_per_step": ms, "bandfluxes_per_s": wl.batch.n_bandflux() / (ms / 1e3),
-        "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3), "kernel": KERNEL_NAMES[fam].format(tile),
-        "achieved_tflops": flops / (ms / 1e3) / 1e12, "grid": [wl.model.n_phase, wl.model.n_wave],
-        "cpu_baseline": sampled_oracle(wl, s, db, stream, n_picks=128)}
-    s.close()
-    del db
-    out["band_files"] = band_file_secondary(dev)
-    from paper_2504_08081_b300 import serving as SV
-    out[W.CONFIG_NAMES[4]] = SV.run_serving_bench(dev.index or 0)
-    out["fit_" + W.CONFIG_NAMES[2]] = fit_secondary(dev, args.cpu_seconds)
-    out["nested_" + W.CONFIG_NAMES[3]] = nested_secondary(dev, args.cpu_seconds)
+        try:
+            with torch.cuda.stream(stream):
+                db = s.upload(wl.batch)
+                torch.cuda.synchronize()
+                durs = time_steps_graph(lambda: s.chi2_grad(db), steps, 2, stream, flush=flush_buf.zero_) or \
+                    time_steps(lambda: s.chi2_grad(db), steps, 2, stream, flush=flush_buf.zero_)
+            ms = statistics.median(durs)
+            fam, tile = s.last_kernel()
+            nbf = wl.batch.n_bandflux()
+            flops = algorithmic_flops(wl, grad=True, max_par=max_par)
+            res = {"ms_per_step": ms, "bandfluxes_per_s": nbf / (ms / 1e3),
+                   "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3), "bandfluxes": nbf,
+                   "samples": wl.batch.n_par, "kernel": KERNEL_NAMES[fam].format(tile),
+                   "grid": [wl.model.n_phase, wl.model.n_wave],
+                   "achieved_tflops": flops / (ms / 1e3) / 1e12}
+            if sampled_pairs:
+                res["cpu_baseline"] = sampled_oracle(wl, s, db, stream, n_picks=sampled_pairs)
+            return res
+        finally:
+            s.close()
+
+    def guarded(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as ex:  # one record's failure must not sink the others
+            out[name] = {"error": repr(ex)}
+
+    for cfg in (3, 5):
+        guarded(W.CONFIG_NAMES[cfg], lambda: timed_workload(make_workload(cfg, 0), 5, 128, max_par=20000))
+
+    def scaled_bench_workload():
+        # the bench workload's shape at 10x the supernovae: how the one-sample
+        # kernel's throughput grows once each warp has many units to run
+        wl = W.config2(seed=1002, n_sn=10000)
+        W.template_flux(wl.batch, np.random.default_rng(1003))
+        return timed_workload(wl, 10, 0)
+    guarded("batched_chi2_10000sn", scaled_bench_workload)
+
+    def nonuniform_grid():
+        # non-uniform (SALT3-NIR-shaped) grid: 66 x 991 nodes, binary-search indexing
+        wl = W.config_nir(n_sn=4000, n_samples=4)
+        W.template_flux(wl.batch, np.random.default_rng(1007))
+        return timed_workload(wl, 10, 128)
+    guarded("nir_nonuniform_4000sn_x4", nonuniform_grid)
+
+    guarded("band_files", lambda: band_file_secondary(dev))
+
+    def serving():
+        from paper_2504_08081_b300 import serving as SV
+        return SV.run_serving_bench(dev.index or 0)
+    guarded(W.CONFIG_NAMES[4], serving)
+    guarded("fit_" + W.CONFIG_NAMES[2], lambda: fit_secondary(dev, args.cpu_seconds))
+    guarded("nested_" + W.CONFIG_NAMES[3], lambda: nested_secondary(dev, args.cpu_seconds))
     return out
 
 
