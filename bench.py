@@ -518,6 +518,10 @@ def nested_secondary(dev, cpu_seconds, n_live=1024, n_batch=256, n_steps=10):
            "likelihood_evals_per_s": evals / wall, "posteriors_per_s": n / wall,
            "logz_err_median": float(np.median(err.cpu().numpy())),
            "timing": "wall clock around salt_nested (it synchronises)"}
+    # counted chi^2-only FLOP per likelihood evaluation (the supernovae at their
+    # truth), times the evaluation rate: the sampler's whole-run FP32 rate
+    per_eval = algorithmic_flops(SimpleNamespace(model=wl.model, bands=wl.bands, batch=tb), grad=False) / n
+    out["achieved_tflops"] = per_eval * evals / wall / 1e12
     s.close()
     o = oracle.Oracle(wl.model, wl.bands)
     t0 = time.perf_counter()
