@@ -124,3 +124,47 @@ def test_invalid_oversized_cancelled_and_unknown(stream):
     rc, _, _ = s.poll(tk, b.n_par, rq.want_grad, wait_ms=0)
     assert rc == -5  # released after it was collected
     s.close()
+
+
+def test_burst_with_cancels_accounts_for_every_request():
+    """A burst of 20 000 requests under a 64 MB budget with 2 % cancelled right
+    after submission: every request ends DONE or CANCELLED, the counters add
+    up, the arenas drain back to empty, and sampled results agree with the
+    batch API's on the same request (to FP32 summation order: the batch call
+    may pick another kernel family or tile)."""
+    import ctypes as C
+    from paper_2504_08081_b300 import _abi, serving as SV
+    wl = W.config4(n_req=20000, seed=4242)
+    reqs = wl.requests
+    s = _salt(wl, serve_mem_bytes=64 << 20)
+    prep = SV._prepared(reqs)
+    L = _abi.lib()
+    rng = np.random.default_rng(1)
+    cancel = rng.random(len(reqs)) < 0.02
+    tks = []
+    for i in range(len(reqs)):
+        req, _, _, _, tk = prep[i]
+        assert L.salt_serve_submit(s.ctx.h, C.byref(req), C.byref(tk)) == _abi.SALT_OK
+        tks.append(tk.value)
+        if cancel[i]:
+            L.salt_serve_cancel(s.ctx.h, tk.value)
+    n_ok = n_cancel = 0
+    for i in range(len(reqs)):
+        _, _, chi2, grad, _ = prep[i]
+        rc = L.salt_serve_poll(s.ctx.h, tks[i], 60000, chi2.ctypes.data,
+                               grad.ctypes.data if grad is not None else None)
+        assert rc in (_abi.SALT_OK, _abi.SALT_ERR_CANCELLED), (i, rc)
+        n_ok += rc == _abi.SALT_OK
+        n_cancel += rc == _abi.SALT_ERR_CANCELLED
+    st = s.serve_stats()
+    assert n_ok + n_cancel == len(reqs) and n_cancel <= int(cancel.sum())
+    assert st["completed"] == n_ok and st["submitted"] == len(reqs)
+    assert st["queued"] == 0 and st["active"] == 0 and st["mem_in_use"] == 0
+    for i in [i for i in rng.choice(len(reqs), 200, replace=False) if not cancel[i]][:100]:
+        x2, g = s.chi2_grad(s.upload(reqs[i].batch, plan=False))
+        np.testing.assert_allclose(prep[i][2], x2.cpu().numpy(), rtol=1e-6)
+        if reqs[i].want_grad:
+            ref = g.cpu().numpy()
+            scale = np.abs(ref).max(axis=1, keepdims=True)
+            assert np.all(np.abs(prep[i][3] - ref) <= 1e-5 * scale)
+    s.close()
