@@ -144,6 +144,24 @@ def test_bitwise_reproducible(cfg3_sub):
     assert torch.equal(s.bandflux(db), bfa)
 
 
+@pytest.mark.parametrize("kernel", ["direct", "factorised", "bandwarp", "unit"])
+def test_bitwise_reproducible_per_kernel(cfg2_sub, kernel):
+    """Every kernel family gives bitwise the same results call after call,
+    whatever order its warps or blocks finish in (fixed summation orders; the
+    warp-unit kernel combines per-band partials in band order)."""
+    wl, _ = cfg2_sub
+    s = _salt(wl)
+    s.set_kernel(KERNELS[kernel])
+    db = s.upload(wl.batch)
+    x2a, ga = (t.clone() for t in s.chi2_grad(db))
+    bfa = s.bandflux(db).clone()
+    for _ in range(5):
+        x2, g = s.chi2_grad(db)
+        assert torch.equal(x2, x2a) and torch.equal(g, ga)
+        assert torch.equal(s.bandflux(db), bfa)
+    s.check()
+
+
 # ------------------------------------------------------------------ edge cases
 
 def _edge_workload():
