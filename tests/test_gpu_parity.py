@@ -3,7 +3,9 @@ same seeded inputs, element by element.
 
 Tolerances: bandflux 1e-5 relative (floor 1e-3 of the supernova's largest
 bandflux); chi^2 within the bound that 1e-5 relative bandflux errors
-propagate to; gradient 1e-3 of the scaled gradient's inf-norm per sample."""
+propagate to; gradient 1e-3 of the scaled gradient's inf-norm per sample, or
+(a sum with cancellation near a minimum) the bound those bandflux errors
+propagate to (tests/_helpers.grad_bound)."""
 import numpy as np
 import pytest
 
@@ -95,7 +97,7 @@ def test_chi2_grad_many_samples(cfg3_sub, kernel, tile):
     ref_x2, ref_g = o.chi2(bt, grad=True)
     ref_bf = o.bandflux(bt)
     H.assert_chi2_close(bt, x2, ref_x2, ref_bf)
-    H.assert_grad_close(bt, g, ref_g)
+    H.assert_grad_close(bt, g, ref_g, o=o, bf_ref=ref_bf)
     # the chi^2 of the gradient call agrees with the chi^2-only call (separately
     # compiled variants: equal up to FP32 contraction order)
     x2b = s.chi2(db).cpu().numpy()
@@ -117,7 +119,7 @@ def test_large_grid_ragged(cfg5_sub, kernel):
     x2, g = s.chi2_grad(db)
     ref_x2, ref_g = o.chi2(bt, grad=True)
     H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
-    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g, o=o, bf_ref=ref_bf)
     s.check()
 
 
@@ -209,7 +211,7 @@ def test_edge_cases(kernel):
     x2, g = s.chi2_grad(db)
     ref_x2, ref_g = o.chi2(bt, grad=True)
     H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
-    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g, o=o, bf_ref=ref_bf)
     # supernova 0 has no observations: chi^2 = 0 and zero gradient exactly
     p0 = slice(bt.par_off[0], bt.par_off[1])
     assert np.all(x2.cpu().numpy()[p0] == 0.0) and np.all(g.cpu().numpy()[p0] == 0.0)
@@ -231,7 +233,7 @@ def test_many_samples_one_supernova(kernel):
                   z=wl.batch.z[idx], x0=wl.batch.x0[idx], x1=wl.batch.x1[idx], c=wl.batch.c[idx])
     ref_x2, ref_g = o.chi2(sub, grad=True)
     H.assert_chi2_close(sub, x2.cpu().numpy()[idx], ref_x2, o.bandflux(sub))
-    H.assert_grad_close(sub, g.cpu().numpy()[idx], ref_g)
+    H.assert_grad_close(sub, g.cpu().numpy()[idx], ref_g, o=o)
 
 
 def test_invalid_data_is_reported():
@@ -325,7 +327,7 @@ def test_observation_passes_overflowing_the_caches(kernel):
     x2, g = s.chi2_grad(db)
     ref_x2, ref_g = o.chi2(bt, grad=True)
     H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
-    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g, o=o, bf_ref=ref_bf)
     s.check()
 
 
@@ -389,7 +391,7 @@ def test_maximum_grid(kernel):
     x2, g = s.chi2_grad(db)
     ref_x2, ref_g = o.chi2(bt, grad=True)
     H.assert_chi2_close(bt, x2.cpu().numpy(), ref_x2, ref_bf)
-    H.assert_grad_close(bt, g.cpu().numpy(), ref_g)
+    H.assert_grad_close(bt, g.cpu().numpy(), ref_g, o=o, bf_ref=ref_bf)
     s.check()
 
 

@@ -81,7 +81,7 @@ def test_serving_matches_oracle():
         x2, g = _result(s, _submit(s, rq), rq)
         ref_x2, ref_g = o.chi2(sub, grad=True)
         H.assert_chi2_close(sub, x2, ref_x2, o.bandflux(sub))
-        H.assert_grad_close(sub, g, ref_g)
+        H.assert_grad_close(sub, g, ref_g, o=o)
     s.close()
 
 
