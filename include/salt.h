@@ -202,8 +202,11 @@ int salt_chi2_grad(salt_ctx *ctx, const salt_batch *batch, double *chi2, float *
                    void *cuda_stream);
 
 /* Synchronise `cuda_stream` and report SALT_ERR_DATA if any kernel since the
- * last salt_check met invalid batch data (the sticky flag is then cleared),
- * SALT_ERR_CUDA on an asynchronous CUDA error, else SALT_OK. */
+ * last salt_check met invalid batch data or produced a non-finite bandflux
+ * from finite parameters (FP32 overflow: a colour factor 10^(-0.4 c CL) or
+ * surface values beyond ~3e38; salt_last_error says which), the sticky flag
+ * then being cleared; SALT_ERR_CUDA on an asynchronous CUDA error; else
+ * SALT_OK. */
 int salt_check(salt_ctx *ctx, void *cuda_stream);
 
 /* ---------------------------------------------------------------- options - */

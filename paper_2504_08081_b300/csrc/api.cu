@@ -826,12 +826,13 @@ extern "C" int salt_check(salt_ctx *ctx, void *cuda_stream) {
     CK(cudaStreamSynchronize(st), "synchronize");
     CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), st), "clear error word");
     CK(cudaStreamSynchronize(st), "synchronize");
-    if (flag & ERRBIT_TIMEOUT)
-        return set_err(ctx, SALT_ERR_TIMEOUT, "a kernel gave up waiting for a shared-memory copy");
     if (flag)
-        return set_err(ctx, SALT_ERR_DATA, (flag & ERRBIT_BAND) ? "a kernel met a band id out of range"
-                                           : (flag & ERRBIT_SIGMA) ? "a kernel met fluxerr <= 0"
-                                                                   : "a kernel met non-finite parameters");
+        return set_err(ctx, SALT_ERR_DATA,
+                       (flag & ERRBIT_BAND)    ? "a kernel met a band id out of range"
+                       : (flag & ERRBIT_SIGMA) ? "a kernel met fluxerr <= 0"
+                       : (flag & ERRBIT_PARAM) ? "a kernel met non-finite parameters"
+                                               : "a bandflux was not finite: FP32 overflow of the colour factor or "
+                                                 "the surfaces (or a non-finite zero point)");
     return SALT_OK;
 }
 

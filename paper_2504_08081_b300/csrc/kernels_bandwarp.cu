@@ -383,6 +383,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                             }
                             const float pre = x0 * a * zpf;
                             const float B = pre * Bs;
+                            if (!isfinite(B)) atomicOr(o.err, ERRBIT_RANGE);
                             if (MODE == MODE_BANDFLUX) {
                                 o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + j) * nobs + (oc + i)] = B;
                             } else {

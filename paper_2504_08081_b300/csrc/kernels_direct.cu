@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(256) k_direct(ModelParams m, BatchDev b, OutDe
         const float zpf = zp_scale(b.zp[i]);
         const float pre = x0 * a * zpf;
         const float B = pre * accB;
+        if (lane == 0 && !isfinite(B)) atomicOr(o.err, ERRBIT_RANGE);
         if (MODE == MODE_BANDFLUX) {
             if (lane == 0) o.bandflux[o.bf_off[s] + jl * (i1 - i0) + (i - i0)] = B;
         } else {

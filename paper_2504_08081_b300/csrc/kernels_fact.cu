@@ -494,6 +494,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     const float zpf = sZpf[i];
                                     const float pre = x0 * a * zpf;
                                     const float B = pre * Bs;
+                                    if (!isfinite(B)) atomicOr(o.err, ERRBIT_RANGE);
                                     if (MODE == MODE_BANDFLUX) {
                                         o.bandflux[wi.bf0 + (int64_t)(jloc0 + j) * nobs + (oc + i)] = B;
                                     } else {

@@ -433,6 +433,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         }
                         const float pre = px0[s] * a * zpf;
                         const float B = pre * Bs;
+                        if (pok[s] && !isfinite(B)) atomicOr(o.err, ERRBIT_RANGE);
                         if (MODE == MODE_BANDFLUX) {
                             o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + s) * nobs + oIdx[il]] = pok[s] ? B : fk::qnanf();
                         } else {

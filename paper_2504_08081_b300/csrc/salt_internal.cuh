@@ -20,7 +20,10 @@
 namespace salt {
 
 // Error bits a kernel records in the context's device error word.
-enum : int { ERRBIT_BAND = 1, ERRBIT_SIGMA = 2, ERRBIT_PARAM = 4, ERRBIT_WINDOW = 8, ERRBIT_TIMEOUT = 16 };
+// Sticky error word bits set by the kernels (read and cleared by salt_check).
+// RANGE: a bandflux came out non-finite from finite parameters (FP32 overflow of
+// the colour factor or the surfaces, or a non-finite zero point).
+enum : int { ERRBIT_BAND = 1, ERRBIT_SIGMA = 2, ERRBIT_PARAM = 4, ERRBIT_RANGE = 8 };
 
 // Band table passed by value to every kernel (fits the kernel parameter space).
 struct BandTable {

@@ -402,3 +402,29 @@ def test_grid_beyond_the_maximum_is_refused():
     assert model.n_phase == 257
     with pytest.raises(SaltError):
         _salt(W.Workload("toolarge", model, [W.gaussian_band(5000.0, 201)], None))
+
+
+def test_fp32_overflow_is_reported():
+    """A colour factor beyond the FP32 range (c = 60 at a rest wavelength where
+    CL is about -2: 10^(48) and more) gives a non-finite bandflux; salt_check
+    reports it as SALT_ERR_DATA and clears the flag, and the other samples are
+    unaffected."""
+    from paper_2504_08081_b300 import SaltError
+    wl = W.config2(n_sn=6)
+    o = H.with_oracle_flux(wl)
+    bt = wl.batch
+    bt.c = bt.c.copy()
+    bt.c[2] = np.float32(60.0)
+    s = _salt(wl)
+    db = s.upload(bt)
+    x2, g = s.chi2_grad(db)
+    x2 = x2.cpu().numpy()
+    assert not np.isfinite(x2[2])
+    with pytest.raises(SaltError) as ei:
+        s.check()
+    assert ei.value.code == -7 and "not finite" in str(ei.value)
+    s.check()  # cleared
+    others = np.arange(bt.n_par) != 2
+    ref_x2 = o.chi2(bt)
+    assert np.all(np.isfinite(x2[others]))
+    np.testing.assert_allclose(x2[others], ref_x2[others], rtol=1e-4)
