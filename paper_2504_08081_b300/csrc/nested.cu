@@ -302,6 +302,12 @@ __global__ void k_propose(Opts op, Dev d, int m) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) d.prop_th[NP * q + i] = th[i];
     d.prop_in[q] = in;
+    // a proposal outside the box is rejected whatever its likelihood: evaluate
+    // the chain's current point in its place, so that no parameter far outside
+    // the prior (a colour factor beyond the FP32 range, say) reaches the kernel
+    if (!in)
+#pragma unroll
+        for (int i = 0; i < NP; ++i) th[i] = d.chain_th[NP * q + i];
     write_eval(d.t0c, d.zc, d.x0c, d.x1c, d.cc, q, th);
 }
 
