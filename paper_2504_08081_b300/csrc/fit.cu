@@ -460,6 +460,14 @@ __global__ void k_fit_update(int n, State *S, const double *chi2, const float *g
     accept_step(st, op, tr, j, ft, gt, n_active);
 }
 
+// Fold the fit's own error word into the context's, without the FP32-range bit:
+// a trial point far out along a search direction may overflow the colour factor,
+// which the line search already treats as "too far".
+__global__ void k_fold_errors(const int *src, int *dst, int mask) {
+    const int v = *src & mask;
+    if (v) atomicOr(dst, v);
+}
+
 __global__ void k_fit_finish(int n, const State *S, Trial tr, double *theta, double *chi2, int *status) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -556,7 +564,7 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     fit::State *S = nullptr;
     double *t0t = nullptr, *chi2 = nullptr;
     float *zt = nullptr, *x0t = nullptr, *x1t = nullptr, *ct = nullptr, *grad = nullptr;
-    int *n_active = nullptr, *counter = nullptr;
+    int *n_active = nullptr, *counter = nullptr, *err_fit = nullptr;
     WorkItem *act = nullptr;  // running fits' work items (warp-unit path)
     void *uscr = nullptr;     // warp-unit kernel scratch
     const bool compact = ctx->mp.n_phase <= unit_max_phase() && ctx->mp.bands.n_bands >= 1;
@@ -572,6 +580,8 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     if (e == cudaSuccess) e = cudaMalloc((void **)&grad, 5 * fb);
     if (e == cudaSuccess) e = cudaMalloc((void **)&n_active, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&err_fit, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err_fit, 0, sizeof(int), st);
     if (e == cudaSuccess && compact) e = cudaMalloc((void **)&act, (size_t)n * sizeof(WorkItem));
     if (e == cudaSuccess && compact) e = cudaMalloc(&uscr, uscr_bytes);
     if (e == cudaSuccess && compact) e = cudaMemsetAsync(uscr, 0, uscr_bytes, st);  // arrival counters
@@ -579,7 +589,7 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     cudaGraphExec_t exec = nullptr;
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
-        void *ptrs[] = {S, t0t, chi2, zt, x0t, x1t, ct, grad, n_active, counter, act, uscr};
+        void *ptrs[] = {S, t0t, chi2, zt, x0t, x1t, ct, grad, n_active, counter, err_fit, act, uscr};
         cudaStreamSynchronize(st);
         for (void *q : ptrs)
             if (q) cudaFree(q);
@@ -600,7 +610,7 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     b.par_off = plan.par_off_d;
     b.mjd = bt->mjd; b.band = bt->band; b.flux = bt->flux; b.fluxerr = bt->fluxerr; b.zp = bt->zp;
     b.t0 = t0t; b.z = zt; b.x0 = x0t; b.x1 = x1t; b.c = ct;
-    const OutDev od{nullptr, plan.bf_off_d, chi2, grad, ctx->err_d};
+    const OutDev od{nullptr, plan.bf_off_d, chi2, grad, err_fit};
 
     fit::k_fit_init<<<(n + 127) / 128, 128, 0, st>>>(n, bt->t0, bt->z, bt->x0, bt->x1, bt->c, lower, upper,
                                                       o.free_mask, S, tr, op, n_active);
@@ -652,6 +662,10 @@ extern "C" int salt_fit(salt_ctx *ctx, const salt_batch *bt, const double *lower
     if (rc == SALT_OK) {
         fit::k_fit_finish<<<(n + 127) / 128, 128, 0, st>>>(n, S, tr, theta, chi2_out, status);
         e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            fit::k_fold_errors<<<1, 1, 0, st>>>(err_fit, ctx->err_d, ~(int)ERRBIT_RANGE);
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) rc = fit_cuda(ctx, e, "fit finish");
     }
     cleanup();
