@@ -1,6 +1,7 @@
-"""Randomized parity sweep: seeded workloads of the three batch shapes (the
-batched 1-sample shape, many samples per supernova, the ragged 71x901 shape)
-with random sizes, every kernel family against the FP64 oracle."""
+"""Randomized parity sweep: seeded workloads of four shapes (the batched
+1-sample shape, many samples per supernova, the ragged 71x901 shape, the
+non-uniform 66x991 grid) with random sizes, every kernel family against the
+FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -15,15 +16,17 @@ KERNELS = {"auto": 0, "direct": 1, "factorised": 2, "bandwarp": 3, "unit": 4}
 
 def _workload(seed):
     rng = np.random.default_rng(seed)
-    kind = seed % 3
+    kind = seed % 4
     if kind == 0:
         return W.config2(seed=5000 + seed, n_sn=int(rng.integers(20, 120)))
     if kind == 1:
         return W.config3(seed=5000 + seed, n_sn=int(rng.integers(2, 6)), n_samples=int(rng.integers(1, 40)))
-    return W.config5(seed=5000 + seed, n_sn=int(rng.integers(10, 50)), n_samples=int(rng.integers(1, 12)))
+    if kind == 2:
+        return W.config5(seed=5000 + seed, n_sn=int(rng.integers(10, 50)), n_samples=int(rng.integers(1, 12)))
+    return W.config_nir(seed=7000 + seed, n_sn=int(rng.integers(5, 40)), n_samples=int(rng.integers(1, 9)))
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(16))
 def test_random_workloads_every_kernel(seed):
     from paper_2504_08081_b300 import build
     build.build()
