@@ -512,7 +512,10 @@ def nested_secondary(dev, cpu_seconds, n_live=1024, n_batch=256, n_steps=10):
     wall = time.perf_counter() - t0
     st = st.cpu().numpy()
     iters = int(st.max())
-    evals = n * (n_live + iters * n_batch * n_steps)
+    # evaluations made: every supernova's live points, then its chains' steps
+    # for the iterations it ran (a stopped supernova's chains are skipped)
+    per_sn_iters = np.where(st >= 0, st, iters)
+    evals = int(n * n_live + per_sn_iters.sum() * n_batch * n_steps)
     out = {"supernovae": n, "n_live": n_live, "n_batch": n_batch, "n_steps": n_steps,
            "wall_s": wall, "iterations_max": iters, "likelihood_evals": evals,
            "likelihood_evals_per_s": evals / wall, "posteriors_per_s": n / wall,

@@ -311,6 +311,13 @@ __global__ void k_propose(Opts op, Dev d, int m) {
     write_eval(d.t0c, d.zc, d.x0c, d.x1c, d.cc, q, th);
 }
 
+// Work items of finished supernovae get no samples, so the chi^2 launches of
+// later iterations skip them (their proposals were never used).
+__global__ void k_drop_done(WorkItem *items, int n_items, const Sn *sn, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_items && sn[items[i].par0 / k].done) items[i].nj = 0;
+}
+
 __global__ void k_accept(Opts op, Dev d) {
     const int s = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= op.n_sn || c >= op.k) return;
@@ -497,10 +504,16 @@ extern "C" int salt_nested(salt_ctx *ctx, const salt_batch *bt, const double *lo
     int P = 1;
     while (P < N) P <<= 1;
     const size_t sel_smem = (size_t)P * (sizeof(double) + sizeof(int));
+    WorkItem *items_c = nullptr;  // the chain plan's work list, once built
+    int n_items_c = 0;
     auto iteration = [&](cudaStream_t s) -> int {
         nsd::k_select<<<n, P, sel_smem, s>>>(op, d);
         cudaError_t e2 = cudaGetLastError();
         if (e2 != cudaSuccess) return ns_cuda(ctx, e2, "nested select");
+        if (items_c) {
+            nsd::k_drop_done<<<(n_items_c + 255) / 256, 256, 0, s>>>(items_c, n_items_c, d.sn, k);
+            if ((e2 = cudaGetLastError()) != cudaSuccess) return ns_cuda(ctx, e2, "nested drop");
+        }
         for (int m = 0; m < M; ++m) {
             nsd::k_propose<<<gc, 128, 0, s>>>(op, d, m);
             if ((e2 = cudaGetLastError()) != cudaSuccess) return ns_cuda(ctx, e2, "nested propose");
@@ -516,6 +529,13 @@ extern "C" int salt_nested(salt_ctx *ctx, const salt_batch *bt, const double *lo
     };
     // first iteration directly (it builds the chain plan's work list), then a captured graph
     if (rc == SALT_OK) rc = iteration(st);
+    if (rc == SALT_OK) {
+        const auto it = plan_c.lists.find(cfg_key(FAM_CTA, tile_c));
+        if (it != plan_c.lists.end()) {
+            items_c = it->second.d;
+            n_items_c = it->second.n;
+        }
+    }
     if (rc == SALT_OK && !ctx->capture_stream &&
         (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
         rc = ns_cuda(ctx, e, "nested stream");
