@@ -289,7 +289,9 @@ int salt_serve_stats_get(salt_ctx *ctx, salt_serve_stats *out);
 #define SALT_FIT_DEFAULT_MASK (SALT_FIT_T0 | SALT_FIT_X0 | SALT_FIT_X1 | SALT_FIT_C)
 
 /* Per-supernova fit outcome (status[s] >= 0: converged after that many
- * accepted steps). */
+ * accepted steps, by gtol, by ftol, or with chi^2 flat to its FP32 resolution,
+ * 2e-6 relative, over eight steps while the quadratic model predicts no larger
+ * decrease). */
 #define SALT_FIT_MAXITER (-1)    /* max_iter steps or max_evals evaluations used */
 #define SALT_FIT_LINESEARCH (-2) /* no step lowers chi^2 any more (at the precision floor) */
 #define SALT_FIT_INVALID (-3)    /* non-finite chi^2 at the start, or an empty box */

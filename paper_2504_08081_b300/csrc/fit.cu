@@ -22,13 +22,15 @@
 //     stays accurate; so, in the manner of approximate Wolfe conditions, a
 //     step that meets the curvature condition is also taken when chi^2 rose
 //     by at most eps, the bracket is steered by the slope's sign wherever
-//     chi^2 differences are within eps, and eight accepted steps in a row that
-//     together lower chi^2 by no more than eps end the fit (converged to the
-//     resolution of chi^2);
-//   - a fit stops when the projected scaled gradient's inf-norm is <= gtol,
-//     when an accepted step lowers chi^2 by <= ftol relative, at max_iter
-//     iterations, or when the line search cannot lower chi^2 any more (after
-//     one retry along steepest descent with the curvature pairs dropped).
+//     chi^2 differences are within eps;
+//   - a fit stops when the projected scaled gradient's inf-norm pg is <= gtol,
+//     at max_iter iterations, or when the line search cannot lower chi^2 any
+//     more (after one retry along steepest descent with the curvature pairs
+//     dropped). When chi^2 stops falling measurably (an accepted step lowers it
+//     by <= ftol relative, or eight in a row together by no more than eps) the
+//     fit has converged to chi^2's resolution if pg <= 100 gtol; with a larger
+//     (accurate) gradient the curvature pairs are dropped instead and the fit
+//     goes on along steepest descent, at most three times.
 // Unlike L-BFGS-B proper there is no generalised Cauchy point or subspace
 // minimisation: bounds enter through the active set and the projection.
 // Blocks of iterations are captured once as a CUDA graph and replayed.
@@ -48,6 +50,8 @@ enum Stage { ST_START = 0, ST_SEARCH = 1, ST_DONE = 2 };
 constexpr double C1 = 1e-4, C2 = 0.9;  // Wolfe constants
 constexpr double NOISE = 2e-6;         // relative chi^2 resolution of the FP32 photometry
 constexpr int QUIET = 8;               // accepted steps without a decrease beyond the noise
+constexpr int RESTARTS = 3;            // flat stretches that restart along steepest descent
+constexpr double FLAT_G = 100.0;       // a flat chi^2 counts as converged when pg <= FLAT_G gtol
 constexpr int LS_MAX = 30;             // evaluations per line search
 
 struct State {
@@ -68,6 +72,7 @@ struct State {
     int iter, nls, evals, stage, status, zoom, has_best;
     int quiet;      // accepted steps since chi^2 last fell by more than the noise
     double f_quiet; // chi^2 when that window began
+    int restarts;   // flat stretches answered by dropping the curvature pairs
 };
 
 struct Opts {
@@ -282,6 +287,7 @@ __global__ void k_fit_init(int n, const double *t0, const float *z, const float 
     st.iter = st.nls = st.evals = 0;
     st.quiet = 0;
     st.f_quiet = INFINITY;
+    st.restarts = 0;
     st.stage = ok ? ST_START : ST_DONE;
     st.status = ok ? 0 : SALT_FIT_INVALID;
     publish(st, tr, j);
@@ -324,10 +330,30 @@ __device__ void accept_step(State &st, const Opts &op, const Trial &tr, int j, d
     } else {
         ++st.quiet;
     }
-    if (pg <= op.gtol || (rel >= 0.0 && rel <= op.ftol) || st.quiet >= QUIET) {
+    if (pg <= op.gtol) {
         st.stage = ST_DONE;
         st.status = st.iter;
-    } else if (st.iter >= op.max_iter || st.evals >= op.max_evals) {
+        return;
+    }
+    if ((rel >= 0.0 && rel <= op.ftol) || st.quiet >= QUIET) {
+        // chi^2 has stopped falling measurably (a step within ftol, or eight
+        // within the noise). That is convergence to its resolution when the
+        // accurate gradient is small too. A large one means the curvature pairs
+        // have gone stale in a curved valley (tiny steps, a tiny inverse-Hessian
+        // scale): drop them and go on along steepest descent, a bounded number
+        // of times.
+        if (pg <= FLAT_G * op.gtol || st.restarts >= RESTARTS) {
+            st.stage = ST_DONE;
+            st.status = st.iter;
+            return;
+        }
+        ++st.restarts;
+        st.quiet = 0;
+        st.f_quiet = st.f;
+        st.count = 0;
+        st.head = 0;
+    }
+    if (st.iter >= op.max_iter || st.evals >= op.max_evals) {
         st.stage = ST_DONE;
         st.status = SALT_FIT_MAXITER;
     } else {
