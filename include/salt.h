@@ -197,7 +197,10 @@ int salt_bandflux(salt_ctx *ctx, const salt_batch *batch, float *out, void *cuda
 int salt_chi2(salt_ctx *ctx, const salt_batch *batch, double *chi2, void *cuda_stream);
 
 /* chi^2 and its gradient d chi^2 / d(z, t0, x0, x1, c) (hand-written adjoint).
- * chi2: DEVICE float64 [n_par]; grad: DEVICE float32 [n_par][5]. */
+ * chi2: DEVICE float64 [n_par]; grad: DEVICE float32 [n_par][5]. A gradient
+ * component beyond the float32 range (|d chi^2/d x0| ~ chi^2 / x0 passes 3.4e38
+ * once chi^2 ~ 1e36 at x0 ~ 1e-5) comes out as +-inf with a finite chi^2;
+ * salt_check does not report it. */
 int salt_chi2_grad(salt_ctx *ctx, const salt_batch *batch, double *chi2, float *grad,
                    void *cuda_stream);
 
