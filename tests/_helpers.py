@@ -148,3 +148,18 @@ def assert_grad_close(batch, got, ref, rtol=GRAD_RTOL, o=None, bf_ref=None):
     worst = float(err.max()) if err.size else 0.0
     assert worst <= 1.0, f"scaled gradient error {worst:.3f} of its allowance (rtol {rtol})"
     return worst
+
+
+DCHI2 = 2e-3  # fit parity: floor of the chi^2 excess allowed over the reference minimum
+
+
+def dchi2_tol(o, start, theta):
+    """Fit parity tolerance per supernova: max(DCHI2, the chi^2 change 1e-5
+    relative bandflux errors can make at theta), theta [n_sn][5]."""
+    out = np.empty(start.n_sn)
+    for s in range(start.n_sn):
+        one = W.subset(start, [s])
+        one.t0 = np.array([theta[s, 1]])
+        one.z, one.x0, one.x1, one.c = (np.array([theta[s, i]]) for i in (0, 2, 3, 4))
+        out[s] = max(DCHI2, chi2_bound(one, o.bandflux(one))[0])
+    return out

@@ -20,19 +20,7 @@ from tests import _helpers as H
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-DCHI2 = 2e-3
-
-
-def dchi2_tol(o, start, theta):
-    """Per supernova: max(DCHI2, chi^2 change 1e-5 relative bandflux errors
-    can make at theta)."""
-    out = np.empty(start.n_sn)
-    for s in range(start.n_sn):
-        one = W.subset(start, [s])
-        one.t0 = np.array([theta[s, 1]])
-        one.z, one.x0, one.x1, one.c = (np.array([theta[s, i]]) for i in (0, 2, 3, 4))
-        out[s] = max(DCHI2, H.chi2_bound(one, o.bandflux(one))[0])
-    return out
+dchi2_tol = H.dchi2_tol
 
 
 def _salt(wl):
