@@ -56,15 +56,20 @@ __device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, c
         const unsigned heads = __ballot_sync(0xffffffffu, head);
         const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of my run
         const int runlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
+        // segmented sums over each run sharing `first`, the 4 tap columns in the
+        // same shuffle rounds (same additions, in the same order, as one at a time)
+        for (int d = 1; d < runlen; d <<= 1) {
+            float y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[q] = __shfl_up_sync(0xffffffffu, v[q], d);
+            if (lane - d >= start)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += y[q];
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            float sv = v[q];
-            for (int d = 1; d < runlen; d <<= 1) {
-                const float y = __shfl_up_sync(0xffffffffu, sv, d);
-                if (lane - d >= start) sv += y;
-            }
             const int col = first + q;
-            if (act && tail && col >= cc && col < cc + W) e0[(col - cc) * estride] += sv;
+            if (act && tail && col >= cc && col < cc + W) e0[(col - cc) * estride] += v[q];
             __syncwarp();
         }
     }
@@ -117,21 +122,29 @@ __device__ __forceinline__ void ebuild3(const ModelParams &m, const float *lam, 
         const unsigned heads = __ballot_sync(0xffffffffu, head);
         const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
         const int runlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
+        // segmented sums over each run of band samples sharing `first`: the runs
+        // are the same for all 4 tap columns, so the 12 values share each shuffle
+        // round (same additions, in the same order, as one column at a time)
+        for (int d = 1; d < runlen; d <<= 1) {
+            float y[3][4];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[e][q] = __shfl_up_sync(0xffffffffu, v[e][q], d);
+            if (lane - d >= start)
+#pragma unroll
+                for (int e = 0; e < 3; ++e)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[e][q] += y[e][q];
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            float s0 = v[0][q], s1 = v[1][q], s2 = v[2][q];
-            for (int d = 1; d < runlen; d <<= 1) {
-                const float y0 = __shfl_up_sync(0xffffffffu, s0, d);
-                const float y1 = __shfl_up_sync(0xffffffffu, s1, d);
-                const float y2 = __shfl_up_sync(0xffffffffu, s2, d);
-                if (lane - d >= start) { s0 += y0; s1 += y1; s2 += y2; }
-            }
             const int col = first + q;
             if (act && tail && col >= cc && col < cc + W) {
                 const int ci = (col - cc) * estride;
-                e0[ci] += s0;
-                e1[ci] += s1;
-                e2[ci] += s2;
+                e0[ci] += v[0][q];
+                e1[ci] += v[1][q];
+                e2[ci] += v[2][q];
             }
             __syncwarp();
         }
