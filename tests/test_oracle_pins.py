@@ -426,3 +426,58 @@ def test_tiny_case_against_50_digit_evaluation():
     trap = lambda y: sum((lw[k + 1] - lw[k]) * (y[k] + y[k + 1]) / 2 for k in range(2))
     ref = trap(g) * mp.power(10, M("0.4") * M(zp)) / trap(zab)
     assert abs(got / float(ref) - 1) < 1e-14
+
+
+# ---------------------------------------------------------------- batched CSR drivers
+
+def _ragged_batch():
+    """A ragged batch whose supernovae have 0, 1 or several observations and
+    0 to 5 parameter samples, with empty supernovae between non-empty ones."""
+    w = W.config2(n_sn=4)
+    rng = np.random.default_rng(11)
+    n_obs = [3, 0, 1, 5, 0, 4, 2, 6, 0]
+    n_par = [2, 3, 0, 1, 0, 5, 4, 0, 2]
+    z = rng.uniform(0.05, 0.5, len(n_obs)).astype(np.float32)
+    bt = W.make_batch(rng, w.model, w.bands, n_obs, z, n_par, perturb=W.PERTURB)
+    W.template_flux(bt, rng)
+    return w, bt
+
+
+def test_batched_drivers_follow_the_per_observation_definition():
+    # The bandflux of observation i of supernova s for its sample j is Eq. 2
+    # evaluated once (om_bandflux_one); the batched drivers only map
+    # (s, j, i) to positions in the CSR layout: bandflux at
+    # bf_off[s] + j n_s + i, chi^2 of sample j the sum of ((f - B)/sigma)^2
+    # over its own supernova's observations and its gradient the sum of
+    # -2 r / sigma dB. Evaluated here one pair at a time from the CSR offsets.
+    w, bt = _ragged_batch()
+    o = oracle.Oracle(w.model, w.bands)
+    bf = o.bandflux(bt)
+    x2, g = o.chi2(bt, grad=True)
+    n_obs = np.diff(bt.obs_off)
+    n_par = np.diff(bt.par_off)
+    assert len(bf) == int(np.sum(n_obs * n_par)) and len(x2) == bt.n_par
+    pos = 0
+    seen_par = 0
+    for s in range(bt.n_sn):
+        for jj in range(int(n_par[s])):
+            j = int(bt.par_off[s]) + jj
+            par = [float(bt.z[j]), float(bt.t0[j]), float(bt.x0[j]), float(bt.x1[j]), float(bt.c[j])]
+            chi, gr = 0.0, np.zeros(5)
+            for i in range(int(n_obs[s])):
+                ob = int(bt.obs_off[s]) + i
+                B, dB = o.bandflux_one(int(bt.band[ob]), float(bt.mjd[ob]), float(bt.zp[ob]), par,
+                                       grad=True)
+                # the stored bandflux sits at the next position of the layout
+                assert bf[pos] == B, (s, jj, i)
+                pos += 1
+                r = (float(bt.flux[ob]) - B) / float(bt.fluxerr[ob])
+                chi += r * r
+                gr += -2.0 * r / float(bt.fluxerr[ob]) * dB
+            # a sample of a supernova without observations has chi^2 = 0, gradient 0
+            assert abs(x2[j] - chi) <= 1e-14 * abs(chi), (s, jj, x2[j], chi)
+            assert np.all(np.abs(g[j] - gr) <= 1e-14 * np.max(np.abs(gr))), (s, jj)
+            seen_par += 1
+    assert pos == len(bf) and seen_par == bt.n_par
+    # the layout really is ragged: some chi^2 are zero (no observations), the rest not
+    assert np.any(x2 == 0.0) and np.all(x2[np.repeat(n_obs, n_par) > 0] > 0.0)
