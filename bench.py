@@ -3,9 +3,10 @@
 One step = one salt_chi2_grad call over the whole batch (phase/wavelength,
 bicubic M0/M1, colour law, band integral, zero point, FP64 chi^2 and the
 adjoint gradient) through the fused persistent factorised kernel. The primary
-workload is the 1000-supernova batched configuration (6 bands, 20-200
-observations, one parameter vector each); inputs are resident in HBM and L2 is
-flushed between timed steps.
+workload is the large ragged batch: 100 000 supernovae x 64 parameter samples,
+observation counts log-uniform in [8, 400] over 8 bands, the 71 x 901 grid,
+z ~ U(0.01, 2) (6.4e8 bandfluxes per step, 0.39 GB of inputs, larger than L2);
+inputs are resident in HBM and L2 is flushed between timed steps as well.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -51,6 +52,7 @@ FLOP_RC_FWD = 4
 FLOP_C_GRAD = 4      # per (sample, band, window column): Q.E_c and Q.E_z
 FLOP_OBS_GRAD = 60   # per (sample, observation): phase taps, 4-row combine, residual, gradient
 FLOP_OBS_FWD = 24
+WORK_SAMPLES = 20000  # samples the FLOP count visits (larger batches: a seeded subsample, scaled)
 
 
 def parse():
@@ -59,7 +61,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 5])
+    ap.add_argument("--n-sn", type=int, default=0,
+                    help="supernovae of the workload (0: its configured size); smaller sizes of the "
+                         "same generator are for profiling captures")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle CPU-baseline budget")
     ap.add_argument("--profile", action="store_true",
@@ -74,9 +79,9 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def make_workload(config: int, rank: int):
+def make_workload(config: int, rank: int, n_sn: int = 0):
     seed = 1000 + config + 7919 * rank
-    wl = W.make(config, seed=seed)
+    wl = W.make(config, seed=seed, **({"n_sn": n_sn} if n_sn else {}))
     W.template_flux(wl.batch, np.random.default_rng(seed + 1))
     return wl
 
@@ -232,7 +237,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    wl = make_workload(args.workload, 0)
+    wl = make_workload(args.workload, 0, args.n_sn)
     bt = wl.batch
     o = oracle.Oracle(wl.model, wl.bands)
     # per step: the first supernovae of the batch up to ~1/4 s of CPU work
@@ -376,22 +381,41 @@ def time_steps(fn, steps, warmup, stream, flush=None, queue_ahead=True):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def sampled_oracle(wl, s, db, stream, n_picks):
-    """The oracle on sampled (supernova, sample) pairs of a batch too large for
-    it: its rate on those pairs, and the error of this library's full-batch
-    results at those pairs against it."""
+def sampled_oracle(wl, s, db, stream, n_picks=None, budget_s=None, results=None):
+    """The oracle on seeded (supernova, sample) pairs of a batch too large for
+    it: its chi^2 + gradient rate on those pairs, and the error of this
+    library's full-batch results at those pairs against it (chi^2 and
+    gradient: `results` = (chi2, grad) device tensors of a timed step, else a
+    new salt_chi2_grad call; bandfluxes: a full-batch salt_bandflux call).
+    The number of pairs is n_picks, or, with budget_s, what fills about that
+    many seconds of oracle time at the rate measured on a first 64 pairs. The
+    first and last sample of the batch are always among them."""
     import torch
     import oracle
     bt = wl.batch
+    o = oracle.Oracle(wl.model, wl.bands)
     rng = np.random.default_rng(77)
-    picks = np.unique(rng.choice(bt.n_par, min(n_picks, bt.n_par), replace=False))
-    sn_of = np.searchsorted(bt.par_off, picks, side="right") - 1
-    sub = W.subset(bt, sn_of)
-    sub.par_off = np.arange(len(picks) + 1, dtype=np.int64)
-    for k in ("t0", "z", "x0", "x1", "c"):
-        setattr(sub, k, getattr(bt, k)[picks].copy())
+
+    def pairs(n):
+        p = rng.choice(bt.n_par, min(n, bt.n_par), replace=False)
+        p = np.unique(np.concatenate([p, [0, bt.n_par - 1]])) if bt.n_par else p
+        sn = np.searchsorted(bt.par_off, p, side="right") - 1
+        sub = W.subset(bt, sn)
+        sub.par_off = np.arange(len(p) + 1, dtype=np.int64)
+        for k in ("t0", "z", "x0", "x1", "c"):
+            setattr(sub, k, getattr(bt, k)[p].copy())
+        return p, sn, sub
+
+    if budget_s is not None:
+        _, _, cal = pairs(64)
+        t0 = time.perf_counter()
+        o.chi2(cal, grad=True)
+        rate = cal.n_bandflux() / max(time.perf_counter() - t0, 1e-6)
+        per_pair = bt.n_bandflux() / max(bt.n_par, 1)
+        n_picks = int(np.clip(budget_s * rate / per_pair, 64, 16384))
+    picks, sn_of, sub = pairs(n_picks)
     with torch.cuda.stream(stream):
-        x2, g = s.chi2_grad(db)
+        x2, g = results if results is not None else s.chi2_grad(db)
         bf = s.bandflux(db)
     torch.cuda.synchronize()
     off = oracle.Oracle.bandflux_offsets(bt)
@@ -401,26 +425,31 @@ def sampled_oracle(wl, s, db, stream, n_picks):
     pk = torch.as_tensor(picks, device=x2.device)
     gpu = (x2[pk].cpu().numpy(), g[pk].cpu().numpy(), bf[torch.as_tensor(idx, device=bf.device)].cpu().numpy())
     del bf
-    o = oracle.Oracle(wl.model, wl.bands)
+    torch.cuda.empty_cache()
     t0 = time.perf_counter()
     rx2, rg = o.chi2(sub, grad=True)
     t = time.perf_counter() - t0
+    share = sub.n_bandflux() / max(bt.n_bandflux(), 1)
     return {"value": sub.n_bandflux() / t, "unit": UNIT, "cores": o.threads, "kind": "oracle",
-            "sample": f"{len(picks)} seeded (supernova, sample) pairs, one sample each, chi2+grad, "
-                      f"FP64 C with OpenMP ({t:.2f} s)",
+            "sample": f"{len(picks)} seeded (supernova, sample) pairs of the batch (the first and last "
+                      f"sample among them; {sub.n_bandflux()} bandfluxes, {share:.2e} of the step), "
+                      f"chi2+grad, FP64 C with OpenMP ({t:.2f} s); the rate is per bandflux, so the "
+                      f"whole step would take the oracle ~{t / share:.0f} s",
+            "cpu_model": cpu_model(),
             "error_vs_oracle": error_vs_oracle(sub, gpu, (rx2, rg, o.bandflux(sub)))}
 
 
-def secondary(args, salt_mod, torch, dev, stream):
+def secondary(args, salt_mod, torch, dev, stream, fp32_peak):
     """Shorter measurements of the other workloads (not the bench line), each
     guarded so that one failing record does not drop the others."""
     from paper_2504_08081_b300.torch_api import Salt
     out = {}
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-    def timed_workload(wl, steps, sampled_pairs, max_par=2_000_000):
+    def timed_workload(wl, steps, sampled_pairs, max_par=2_000_000, full_oracle=False):
         """chi^2 + gradient steps of a workload (graph-timed, L2 flushed), its
-        counted FLOP rate and, optionally, sampled errors against the oracle."""
+        counted FLOP rate against the FP32 peak and, optionally, errors against
+        the oracle on sampled pairs or on every output."""
         s = Salt(wl.model, wl.bands, device=dev.index or 0)
         try:
             with torch.cuda.stream(stream):
@@ -436,9 +465,17 @@ def secondary(args, salt_mod, torch, dev, stream):
                    "chi2_grad_evals_per_s": wl.batch.n_par / (ms / 1e3), "bandfluxes": nbf,
                    "samples": wl.batch.n_par, "kernel": KERNEL_NAMES[fam].format(tile),
                    "grid": [wl.model.n_phase, wl.model.n_wave],
-                   "achieved_tflops": flops / (ms / 1e3) / 1e12}
+                   "achieved_tflops": flops / (ms / 1e3) / 1e12,
+                   "frac_fp32": flops / (ms / 1e3) / 1e12 / fp32_peak}
             if sampled_pairs:
                 res["cpu_baseline"] = sampled_oracle(wl, s, db, stream, n_picks=sampled_pairs)
+            if full_oracle:
+                with torch.cuda.stream(stream):
+                    x2, g = s.chi2_grad(db)
+                    bf = s.bandflux(db)
+                torch.cuda.synchronize()
+                res["cpu_baseline"] = cpu_baseline(wl, 2.0, gpu=(x2.cpu().numpy(), g.cpu().numpy(),
+                                                                 bf.cpu().numpy()))
             return res
         finally:
             s.close()
@@ -449,8 +486,10 @@ def secondary(args, salt_mod, torch, dev, stream):
         except Exception as ex:  # one record's failure must not sink the others
             out[name] = {"error": repr(ex)}
 
-    for cfg in (3, 5):
-        guarded(W.CONFIG_NAMES[cfg], lambda: timed_workload(make_workload(cfg, 0), 5, 128, max_par=20000))
+    # the 1000-supernova batched configuration (one sample each; every output
+    # against the oracle) and the 256 x 1024 differentiation batch
+    guarded(W.CONFIG_NAMES[2], lambda: timed_workload(make_workload(2, 0), 20, 0, full_oracle=True))
+    guarded(W.CONFIG_NAMES[3], lambda: timed_workload(make_workload(3, 0), 5, 128, max_par=20000))
 
     def scaled_bench_workload():
         # the bench workload's shape at 10x the supernovae: how the one-sample
@@ -633,7 +672,7 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    wl = make_workload(args.workload, rank)
+    wl = make_workload(args.workload, rank, args.n_sn)
     bt = wl.batch
     stream = torch.cuda.Stream(dev)
     salt = Salt(wl.model, wl.bands, device=local_rank)
@@ -767,7 +806,9 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (the one the plan launched)
     fam, tile = salt.last_kernel()
-    flops, grid_bytes = algorithmic_work(wl, grad=True)
+    flops, grid_bytes = algorithmic_work(wl, grad=True, max_par=WORK_SAMPLES)
+    work_how = ("exact count over every sample" if bt.n_par <= WORK_SAMPLES else
+                f"counted over {WORK_SAMPLES} seeded samples of {bt.n_par}, scaled by their share")
     clocks = clk.summary()
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -790,7 +831,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / fp32_peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": KERNEL_NAMES[fam].format(tile),
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                "flop_per_launch": flops,
+                "flop_per_launch": flops, "flop_count": work_how,
                 "ncu_counters": measured_counters(kname, W.CONFIG_NAMES[args.workload]),
                 "peak_check": peak_check}
     # the same launch against the measured L2 read bandwidth: the grid values
@@ -803,18 +844,22 @@ def run_ours(args, rank, world, local_rank):
                             "per (sample, band)", "peak_source": "salt_measure_peaks (measured)"}
 
     # ---- CPU baseline: the oracle as it stands, on the host cores, and the
-    # error of this step's results (and of a bandflux call) against its results
-    with torch.cuda.stream(stream):
-        bf_gpu = salt.bandflux(db)
-    torch.cuda.synchronize()
-    cpu = cpu_baseline(wl, args.cpu_seconds,
-                       gpu=(chi2.cpu().numpy(), grad.cpu().numpy(), bf_gpu.cpu().numpy()))
-    del bf_gpu
+    # error of this step's results (and of a bandflux call) against its results:
+    # whole passes of a batch it finishes in seconds, else seeded sampled pairs
+    if bt.n_bandflux() <= 2_000_000:
+        with torch.cuda.stream(stream):
+            bf_gpu = salt.bandflux(db)
+        torch.cuda.synchronize()
+        cpu = cpu_baseline(wl, args.cpu_seconds,
+                           gpu=(chi2.cpu().numpy(), grad.cpu().numpy(), bf_gpu.cpu().numpy()))
+        del bf_gpu
+    else:
+        cpu = sampled_oracle(wl, salt, db, stream, budget_s=args.cpu_seconds, results=(chi2, grad))
 
     extras = {}
     if world == 1 and not args.no_extras:
         try:
-            extras = secondary(args, None, torch, dev, stream)
+            extras = secondary(args, None, torch, dev, stream, fp32_peak)
         except Exception as ex:  # secondary numbers must not sink the bench line
             extras = {"error": repr(ex)}
 
@@ -827,7 +872,10 @@ def run_ours(args, rank, world, local_rank):
                    "bandfluxes_per_step": int(n_bf_all), "samples_per_step": int(n_par_all),
                    "bands": len(wl.bands), "grid": [wl.model.n_phase, wl.model.n_wave],
                    "step": "salt_chi2_grad (chi2 + adjoint gradient)",
-                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "input_bytes": int(h2d),
+                   "l2": "flushed between steps (256 MB write outside the timed events)" +
+                         (f"; the inputs ({h2d / 1e9:.2f} GB) are larger than L2 as well"
+                          if h2d > 126e6 else ""),
                    "timing": timing,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "chi2_grad_evals_per_s": n_par_all / (ms_max / 1e3),
@@ -864,10 +912,10 @@ def measured_traffic(kernel, workload):
     import hashlib
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
     try:
-        rec = json.load(open(path)).get(kernel)
+        rec = json.load(open(path)).get(f"{kernel} @ {workload}")
     except (OSError, ValueError):
         return None, "no capture"
-    if not rec or rec.get("workload") != workload:
+    if not rec:
         return None, "no capture of this kernel on this workload"
     h = hashlib.sha256()
     root = os.path.dirname(os.path.abspath(__file__))
@@ -885,7 +933,7 @@ def measured_counters(kernel, workload):
     if traffic is None:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
-    return json.load(open(path)).get(kernel, {}).get("counters")
+    return json.load(open(path)).get(f"{kernel} @ {workload}", {}).get("counters")
 
 
 def cpu_baseline(wl, budget_s, gpu=None):

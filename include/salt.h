@@ -291,13 +291,18 @@ int salt_serve_stats_get(salt_ctx *ctx, salt_serve_stats *out);
 #define SALT_FIT_C 16
 #define SALT_FIT_DEFAULT_MASK (SALT_FIT_T0 | SALT_FIT_X0 | SALT_FIT_X1 | SALT_FIT_C)
 
-/* Per-supernova fit outcome (status[s] >= 0: converged after that many
- * accepted steps, by gtol, by ftol, or with chi^2 flat to its FP32 resolution,
- * 2e-6 relative, over eight steps while the quadratic model predicts no larger
- * decrease). */
+/* Per-supernova fit outcome. status[s] >= 0: converged after that many
+ * accepted steps, either with the projected scaled gradient's inf-norm pg
+ * <= gtol, or with chi^2 flat (an accepted step lowering it by <= ftol
+ * relative, or eight in a row lowering it together by no more than its FP32
+ * resolution, 2e-6 relative) while pg <= 100 gtol. A flat chi^2 with a larger
+ * pg drops the L-BFGS curvature pairs and goes on along steepest descent; the
+ * fourth such flat stretch ends the fit with SALT_FIT_FLAT. */
 #define SALT_FIT_MAXITER (-1)    /* max_iter steps or max_evals evaluations used */
 #define SALT_FIT_LINESEARCH (-2) /* no step lowers chi^2 any more (at the precision floor) */
 #define SALT_FIT_INVALID (-3)    /* non-finite chi^2 at the start, or an empty box */
+#define SALT_FIT_FLAT (-4)       /* chi^2 flat after three steepest-descent restarts while
+                                    pg stayed above 100 gtol: stopped, not converged */
 
 /* Options of salt_fit; zero fields take the defaults. */
 typedef struct {
@@ -307,8 +312,9 @@ typedef struct {
     int32_t free_mask;  /* SALT_FIT_* bits of the fitted parameters (default t0, x0, x1, c) */
     double gtol;        /* stop when the inf-norm of the projected gradient in scaled
                            variables is <= gtol (default 1e-3) */
-    double ftol;        /* or when an accepted step lowers chi^2 by <= ftol relative
-                           (default 1e-10) */
+    double ftol;        /* an accepted step lowering chi^2 by <= ftol relative counts as
+                           a flat chi^2 (default 1e-10): the fit ends there only if
+                           pg <= 100 gtol (see the statuses above) */
 } salt_fit_opts;
 
 /* Fit the SALT parameters of every supernova of a batch independently by
@@ -400,8 +406,10 @@ int salt_nested(salt_ctx *ctx, const salt_batch *batch, const double *lower, con
  * (about 39,000 samples with 6 bands) and returns SALT_ERR_INVALID, touching
  * nothing, if that exceeds SALT_NOALLOC_SCRATCH_BYTES or if the model has more
  * than 128 phase nodes; salt_last_error gives the bytes needed. Each call
- * copies the HOST offsets into the array and clears the counters that must
- * start at zero, on cuda_stream.
+ * copies the HOST offsets (pageable memory, cudaMemcpyAsync) into the array
+ * and clears the counters that must start at zero, on cuda_stream. With
+ * batch->validate set it synchronises cuda_stream to read the verdict, and
+ * returns SALT_ERR_INVALID, touching nothing, while cuda_stream is capturing.
  * The first call on each device looks the array's address up
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * The array is shared by every call on that device in the process: two calls

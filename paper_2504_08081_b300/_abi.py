@@ -49,7 +49,7 @@ EXPORTS = [
 # Fitting (salt_fit): parameter bits, outcome codes.
 SALT_FIT_Z, SALT_FIT_T0, SALT_FIT_X0, SALT_FIT_X1, SALT_FIT_C = 1, 2, 4, 8, 16
 SALT_FIT_DEFAULT_MASK = SALT_FIT_T0 | SALT_FIT_X0 | SALT_FIT_X1 | SALT_FIT_C
-SALT_FIT_MAXITER, SALT_FIT_LINESEARCH, SALT_FIT_INVALID = -1, -2, -3
+SALT_FIT_MAXITER, SALT_FIT_LINESEARCH, SALT_FIT_INVALID, SALT_FIT_FLAT = -1, -2, -3, -4
 
 # Scratch bytes of the no-allocation call (SALT_NOALLOC_SCRATCH_BYTES).
 SALT_NOALLOC_SCRATCH_BYTES = 16 << 20

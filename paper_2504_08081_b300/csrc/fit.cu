@@ -30,7 +30,8 @@
 //     by <= ftol relative, or eight in a row together by no more than eps) the
 //     fit has converged to chi^2's resolution if pg <= 100 gtol; with a larger
 //     (accurate) gradient the curvature pairs are dropped instead and the fit
-//     goes on along steepest descent, at most three times.
+//     goes on along steepest descent, at most three times; a fit still flat
+//     with pg > 100 gtol after that ends with SALT_FIT_FLAT, not as converged.
 // Unlike L-BFGS-B proper there is no generalised Cauchy point or subspace
 // minimisation: bounds enter through the active set and the projection.
 // Blocks of iterations are captured once as a CUDA graph and replayed.
@@ -343,8 +344,9 @@ __device__ void accept_step(State &st, const Opts &op, const Trial &tr, int j, d
         // scale): drop them and go on along steepest descent, a bounded number
         // of times.
         if (pg <= FLAT_G * op.gtol || st.restarts >= RESTARTS) {
+            // restarts used up with the gradient still large: stopped, not converged
             st.stage = ST_DONE;
-            st.status = st.iter;
+            st.status = pg <= FLAT_G * op.gtol ? st.iter : SALT_FIT_FLAT;
             return;
         }
         ++st.restarts;

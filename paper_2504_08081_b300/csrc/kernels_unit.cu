@@ -523,11 +523,15 @@ static cudaError_t launch_uk(const salt_ctx *ctx, const WorkItem *items_d, int n
                              void *scratch, const BatchDev &b, const OutDev &o, cudaStream_t st,
                              const int *n_items_dev) {
     const size_t smem = uk::Lay(TS, MODE == MODE_GRAD, ctx->mp.n_phase).total;
+    // once per (device, instantiation): opt in at the size of the largest model
+    // the kernel takes (NPHW phase nodes), so that contexts with more phase
+    // nodes than the first one launched stay within the opted-in limit
     static std::atomic<int> attr_done[64];
     cudaError_t e;
     const int dv = ctx->device & 63;
     if (!attr_done[dv].load()) {
-        e = cudaFuncSetAttribute(uk::k_unit<TS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(uk::k_unit<TS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)uk::Lay(TS, MODE == MODE_GRAD, uk::NPHW).total);
         if (e != cudaSuccess) return e;
         attr_done[dv].store(1);
     }

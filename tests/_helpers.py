@@ -129,11 +129,26 @@ def grad_bound(batch, bf_ref, jac, rtol=BF_RTOL):
     return out
 
 
-def assert_grad_close(batch, got, ref, rtol=GRAD_RTOL, o=None, bf_ref=None):
+# Samples whose gradient may pass only through grad_bound (the fallback): at
+# most FALLBACK_FRAC of a batch's samples, and at least FALLBACK_MIN allowed.
+FALLBACK_FRAC = 0.01
+FALLBACK_MIN = 2
+# (test, samples compared, samples that needed the fallback) of every call
+FALLBACK_LOG = []
+
+
+def assert_grad_close(batch, got, ref, rtol=GRAD_RTOL, o=None, bf_ref=None, max_fallback=None):
     """Scaled gradient within rtol of its per-sample inf-norm; where that fails
     and the oracle `o` is given, within the larger of that and grad_bound (what
     the bandflux tolerance allows a gradient that is a sum with cancellation,
-    near a minimum) -- the gradient counterpart of assert_chi2_close."""
+    near a minimum) -- the gradient counterpart of assert_chi2_close.
+
+    At most `max_fallback` samples may pass through grad_bound alone
+    (default: max(FALLBACK_MIN, ceil(FALLBACK_FRAC * samples))), so that a
+    regression moving many gradients into the fallback fails. Returns
+    (worst error as a fraction of its allowance, samples that needed the
+    fallback); every call is recorded in FALLBACK_LOG."""
+    import os
     s = grad_scale(batch)
     gs = np.asarray(got, np.float64) * s
     rs = np.asarray(ref, np.float64) * s
@@ -141,13 +156,21 @@ def assert_grad_close(batch, got, ref, rtol=GRAD_RTOL, o=None, bf_ref=None):
     norm = np.max(np.abs(rs), axis=1, keepdims=True)
     allowed = rtol * np.maximum(norm, 1e-300)
     err = np.abs(gs - rs) / allowed
-    if err.size and err.max() > 1.0 and o is not None:
+    strict_fail = err.max(axis=1) > 1.0 if err.size else np.zeros(0, bool)
+    n_fallback = 0
+    if strict_fail.any() and o is not None:
         bf = o.bandflux(batch) if bf_ref is None else bf_ref
         bound = grad_bound(batch, bf, bandflux_jacobian(o, batch)) * s
         err = np.abs(gs - rs) / np.maximum(allowed, bound)
+        n_fallback = int(np.sum(strict_fail & (err.max(axis=1) <= 1.0)))
     worst = float(err.max()) if err.size else 0.0
+    n = int(gs.shape[0])
+    FALLBACK_LOG.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], n, n_fallback))
     assert worst <= 1.0, f"scaled gradient error {worst:.3f} of its allowance (rtol {rtol})"
-    return worst
+    limit = max(FALLBACK_MIN, int(np.ceil(FALLBACK_FRAC * n))) if max_fallback is None else max_fallback
+    assert n_fallback <= limit, \
+        f"{n_fallback} of {n} gradients pass only through the bandflux-derived bound (limit {limit})"
+    return worst, n_fallback
 
 
 DCHI2 = 2e-3  # fit parity: floor of the chi^2 excess allowed over the reference minimum

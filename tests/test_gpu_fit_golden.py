@@ -99,7 +99,7 @@ def test_device_fits_reach_the_stored_minima(golden, mode):
     tol = H.dchi2_tol(o, start, ref_th)
     assert np.all(f_at - ref_f <= tol), (f_at - ref_f - tol).max()
     assert np.all(f_at - ref_f >= -tol), (ref_f - f_at - tol).max()
-    assert np.all((st >= 0) | (st == -2)), st
+    assert np.all((st >= 0) | (st == -2) | (st == -4)), st  # converged or at the FP32 floor
     if mode == 1:
         assert np.all(th[:, 0] >= lower[:, 0]) and np.all(th[:, 0] <= upper[:, 0])
     else:

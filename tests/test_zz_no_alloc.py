@@ -36,7 +36,7 @@ def _grad_close(got, ref):
 @pytest.mark.parametrize("which", ["one_sample_per_sn", "many_samples_per_sn"])
 def test_noalloc_matches_chi2_grad_on_two_calls(which):
     wl = W.config2(n_sn=300) if which == "one_sample_per_sn" else W.config3(n_sn=7, n_samples=45)
-    H.with_oracle_flux(wl)
+    o = H.with_oracle_flux(wl)
     s = _salt(wl)
     db = s.upload(wl.batch)
     n = db.n_par
@@ -63,6 +63,34 @@ def test_noalloc_matches_chi2_grad_on_two_calls(which):
         _grad_close(g, ga)
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    # and directly against the FP64 oracle, within the parity tolerances
+    ref_x2, ref_g = o.chi2(wl.batch, grad=True)
+    ref_bf = o.bandflux(wl.batch)
+    H.assert_chi2_close(wl.batch, outs[1][0], ref_x2, ref_bf)
+    H.assert_grad_close(wl.batch, outs[1][1], ref_g, o=o, bf_ref=ref_bf)
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    """After a first call (which looks the scratch array's address up), a
+    further call leaves the device's free memory unchanged: the scratch is the
+    library's fixed array, nothing is allocated for the call."""
+    wl = W.config2(n_sn=200)
+    H.with_oracle_flux(wl)
+    s = _salt(wl)
+    db = s.upload(wl.batch, plan=False)
+    n = db.n_par
+    x2 = torch.empty(n, dtype=torch.float64, device=s.device)
+    g = torch.empty((n, 5), dtype=torch.float32, device=s.device)
+    s.chi2_grad_noalloc(db, x2, g)
+    torch.cuda.synchronize()
+    free = []
+    for _ in range(3):
+        before = torch.cuda.mem_get_info(s.device)[0]
+        s.chi2_grad_noalloc(db, x2, g)
+        torch.cuda.synchronize()
+        free.append((before, torch.cuda.mem_get_info(s.device)[0]))
+    s.check()
+    assert all(b == a for b, a in free), free
 
 
 def test_noalloc_rejects_a_batch_beyond_its_scratch():
