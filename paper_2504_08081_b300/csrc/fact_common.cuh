@@ -16,6 +16,103 @@ __device__ __forceinline__ int first_tap(int iv, int n) {
     return iv == 0 ? 0 : (iv == n - 2 ? n - 4 : iv - 1);
 }
 
+// 2^x by the special-function unit (PTX ex2.approx.ftz.f32, relative error
+// about 2^-22 over the normal range). The colour factors 10^(-0.4 c CL) it
+// serves are far from the denormal range, where exp2f's extra scaling steps
+// would matter.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One band sample's contribution to the column response: its first tap column
+// and the 4 weighted taps w_k C_k psi_m(lambda'_k) (rest wavelength a lambda_k).
+__device__ __forceinline__ void ebuild_point(const ModelParams &m, const float *lam, const float *wk, int k, float a,
+                                             float c, int &first, float (&v)[4]) {
+    const float lr = lam[k] * a;
+    int iv;
+    float t, iw;
+    wave_find(m, lr, iv, t, iw);
+    Taps4 tl;
+    axis_taps_from<false>(iv, t, m.n_wave, iw, tl);
+    float dcl;
+    const float cl = colour_law(m, lr, dcl);
+    const float A = wk[k] * ex2_approx(kColour * c * cl);
+    first = tl.first;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = A * tl.w[q];
+}
+
+// The column-response build of ebuild with two consecutive band samples per
+// lane (k = k0 + 2 lane and k0 + 2 lane + 1, chunks of 64 strided by
+// `stride`): a lane whose two samples share their first tap column adds them
+// locally; a lane whose pair straddles two columns hands its first sample to
+// the previous lane when that lane's run has the same first column (the run
+// then ends there), and otherwise writes it alone after the main pass. The
+// segmented scan and the column writes then run once per 64 band samples.
+// Columns `estride` apart from e0 (column cc).
+__device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *lam, const float *wk, int kl,
+                                            int k_begin, int stride, float a, float c, int cc, int W, int lane,
+                                            float *e0, int estride) {
+    for (int k0 = k_begin; k0 <= kl; k0 += stride) {
+        const int ka = k0 + 2 * lane, kb = ka + 1;
+        const bool acta = ka <= kl, actb = kb <= kl;
+        int fa = 0x40000000 + 2 * lane, fb = fa + 1;  // inactive: keys of their own, never written
+        float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
+        if (acta) ebuild_point(m, lam, wk, ka, a, c, fa, va);
+        if (actb) ebuild_point(m, lam, wk, kb, a, c, fb, vb);
+        const bool split = actb && fa != fb;  // (then acta as well)
+        const int key = actb ? fb : fa;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (actb && !split) ? va[q] + vb[q] : (actb ? vb[q] : va[q]);
+        // a straddling pair's first sample joins the previous lane's run when
+        // that run has its first column
+        const int prevkey = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool give = split && lane > 0 && prevkey == fa;
+        const bool alone = split && !give;
+        const bool take = __shfl_down_sync(0xffffffffu, (int)give, 1) != 0 && lane < 31;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float y = __shfl_down_sync(0xffffffffu, va[q], 1);
+            if (take) v[q] += y;
+        }
+        const bool act = acta || actb;
+        const int fprev = __shfl_up_sync(0xffffffffu, key, 1);
+        const int fnext = __shfl_down_sync(0xffffffffu, key, 1);
+        const bool head = lane == 0 || fprev != key;
+        const bool tail = lane == 31 || fnext != key;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const int runlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
+        for (int d = 1; d < runlen; d <<= 1) {
+            float y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[q] = __shfl_up_sync(0xffffffffu, v[q], d);
+            if (lane - d >= start)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += y[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int col = key + q;
+            if (act && tail && col >= cc && col < cc + W) e0[(col - cc) * estride] += v[q];
+            __syncwarp();
+        }
+        // first samples that stand alone (a run of one band sample, or the
+        // chunk's first lane continuing the previous chunk's run)
+        if (__any_sync(0xffffffffu, alone)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int col = fa + q;
+                if (alone && col >= cc && col < cc + W) e0[(col - cc) * estride] += va[q];
+                __syncwarp();
+            }
+        }
+    }
+}
+
 // Column-response build for one sample over band samples [kf, kl], columns
 // [cc, cc + W) of the current chunk, by one warp (chunks of 32 band samples
 // strided by `stride`). Per band sample k (one per lane): rest wavelength,
@@ -44,7 +141,7 @@ __device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, c
             axis_taps_from<false>(iv, t, NW, iw, tl);
             float dcl;
             const float cl = colour_law(m, lr, dcl);
-            const float A = wk[k] * exp2f(kColour * c * cl);
+            const float A = wk[k] * ex2_approx(kColour * c * cl);
             first = tl.first;
 #pragma unroll
             for (int q = 0; q < 4; ++q) v[q] = A * tl.w[q];
@@ -79,10 +176,11 @@ __device__ __forceinline__ void ebuild(const ModelParams &m, const float *lam, c
 //   E_c[col] = sum_k dA_k/dc psi_col(t_k)                          (d E / d c)
 //   E_z[col] = sum_k dlambda'_k/dz (A_k psi'_col + dA_k/dlambda' psi_col)   (d E / d z through lambda')
 // (A_k = w_k C_k), built with the same segmented scan. e0/e1/e2 point at
-// column cc of E, E_c, E_z, columns `estride` apart.
+// column cc of E, E_c, E_z, columns `estride` apart in E and `estride12`
+// apart in E_c and E_z (the same as in E when estride12 is 0).
 __device__ __forceinline__ void ebuild3(const ModelParams &m, const float *lam, const float *wk, int kl, int k_begin,
                                         int stride, float a, float c, int cc, int W, int lane, float *e0, float *e1,
-                                        float *e2, int estride) {
+                                        float *e2, int estride, int estride12 = 0) {
     const int NW = m.n_wave;
     for (int k0 = k_begin; k0 <= kl; k0 += stride) {
         const int k = k0 + lane;
@@ -103,7 +201,7 @@ __device__ __forceinline__ void ebuild3(const ModelParams &m, const float *lam, 
             axis_taps_from<true>(iv, t, NW, iw, tl);
             float dcl;
             const float cl = colour_law(m, lr, dcl);
-            const float A = wk[k] * exp2f(kColour * c * cl);
+            const float A = wk[k] * ex2_approx(kColour * c * cl);
             const float Ac = A * (kColourLn * cl);
             const float Zs = -A * lr * a;
             const float Zv = Zs * (kColourLn * c * dcl);
@@ -142,9 +240,10 @@ __device__ __forceinline__ void ebuild3(const ModelParams &m, const float *lam, 
             const int col = first + q;
             if (act && tail && col >= cc && col < cc + W) {
                 const int ci = (col - cc) * estride;
+                const int ci12 = estride12 ? (col - cc) * estride12 : ci;
                 e0[ci] += v[0][q];
-                e1[ci] += v[1][q];
-                e2[ci] += v[2][q];
+                e1[ci12] += v[1][q];
+                e2[ci12] += v[2][q];
             }
             __syncwarp();
         }
@@ -170,19 +269,37 @@ __device__ __forceinline__ void eadjoint(const ModelParams &m, const float *lam,
         float t;
         float iw;
             wave_find(m, lr, iv, t, iw);
-        Taps4 tl;
-        axis_taps_from<true>(iv, t, NW, iw, tl);
-        float dcl;
-        const float cl = colour_law(m, lr, dcl);
-        const float A = wk[k] * exp2f(kColour * c * cl);
-        float qs = 0.f, qd = 0.f;
+        // Q interpolated at lambda'_k and its slope: on an interior interval the
+        // Keys a = -1/2 (Catmull-Rom) cubic through Q at nodes iv-1 .. iv+2,
+        //   Q1 + t (Q2 - Q0)/2 + t^2 (Q0 - 5/2 Q1 + 2 Q2 - Q3/2)
+        //      + t^3 ((Q3 - Q0)/2 + 3/2 (Q1 - Q2)),
+        // on the first / last interval the straight line through its two nodes
+        const int first = first_tap(iv, NW);
+        float qv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int col = tl.first + q - cc;
-            const float qv = (col >= 0 && col < W) ? Q[col * qstride] : 0.f;
-            qs = fmaf(tl.w[q], qv, qs);
-            qd = fmaf(tl.dw[q], qv, qd);
+            const int col = first + q - cc;
+            qv[q] = (col >= 0 && col < W) ? Q[col * qstride] : 0.f;
         }
+        const bool lo = iv == 0, hi = iv == NW - 2;
+        float c0, c1, c2, c3;
+        if (lo || hi) {
+            const float p0 = lo ? qv[0] : qv[2], p1 = lo ? qv[1] : qv[3];
+            c0 = p0;
+            c1 = p1 - p0;
+            c2 = 0.f;
+            c3 = 0.f;
+        } else {
+            c0 = qv[1];
+            c1 = 0.5f * (qv[2] - qv[0]);
+            c2 = fmaf(-0.5f, qv[3], fmaf(2.0f, qv[2], fmaf(-2.5f, qv[1], qv[0])));
+            c3 = fmaf(0.5f, qv[3] - qv[0], 1.5f * (qv[1] - qv[2]));
+        }
+        const float qs = fmaf(fmaf(fmaf(c3, t, c2), t, c1), t, c0);
+        const float qd = fmaf(fmaf(3.0f * c3, t, 2.0f * c2), t, c1) * iw;
+        float dcl;
+        const float cl = colour_law(m, lr, dcl);
+        const float A = wk[k] * ex2_approx(kColour * c * cl);
         const float Zs = -A * lr * a;  // d lambda'/dz = -lambda' a
         gc = fmaf(A * (kColourLn * cl), qs, gc);
         gz = fmaf(Zs, fmaf(kColourLn * c * dcl, qs, qd), gz);

@@ -408,8 +408,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                 const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
                                 float *e0 = (WPS == 1) ? sE + j : sEp + warp * WMAX;
-                                ebuild(m, lam, wk, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane, e0,
-                                       (WPS == 1) ? TJ : 1);
+                                ebuild_pair(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, e0,
+                                            (WPS == 1) ? TJ : 1);
                             }
                         }
                         __syncthreads();
