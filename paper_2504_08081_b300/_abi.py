@@ -113,6 +113,39 @@ class Peaks(C.Structure):
                 ("sm_clock_max_mhz", C.c_double), ("num_sms", C.c_int32)]
 
 
+class ReplayStats(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("submit_s", C.c_double), ("completed", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
+class PlainStats(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("completed", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
+CLIENT_EXPORTS = ("salt_client_replay", "salt_client_plain")
+_client = None
+
+
+def client():
+    """Load libsalt_client.so, the native load generator over the C ABI
+    (salt_client.h); raises if it has not been built."""
+    global _client
+    if _client is not None:
+        return _client
+    lib()  # the client links the library: load it (and its checks) first
+    path = os.path.join(os.path.dirname(LIB_PATH), "libsalt_client.so")
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_2504_08081_b300/build.py")
+    L = C.CDLL(path)
+    p = C.c_void_p
+    L.salt_client_replay.argtypes = [p, p, C.c_int32, p, p, p, p, C.POINTER(ReplayStats)]
+    L.salt_client_replay.restype = C.c_int
+    L.salt_client_plain.argtypes = [p, p, C.c_int32, C.c_double, C.c_size_t, p, C.POINTER(PlainStats)]
+    L.salt_client_plain.restype = C.c_int
+    _client = L
+    return L
+
+
 _lib = None
 
 

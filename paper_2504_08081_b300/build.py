@@ -9,6 +9,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libsalt_b300.so")
+CLIENT_SRC = os.path.join(PKG, "client", "client.cpp")
+CLIENT_LIB = os.path.join(PKG, "libsalt_client.so")
 BUILD = os.path.join(ROOT, "_build")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -49,6 +51,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
         os.replace(LIB + ".tmp", LIB)
+    # the native load generator (salt_client.h), linked against the library
+    if force or _stale(CLIENT_LIB, [CLIENT_SRC, LIB, os.path.join(INCLUDE, "salt_client.h")]):
+        cmd = [NVCC, *ARCH, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-I", INCLUDE,
+               "-shared", CLIENT_SRC, "-o", CLIENT_LIB + ".tmp", "-L", PKG, "-lsalt_b300", "-lcudart", "-lpthread",
+               "-Xlinker", "-rpath,$ORIGIN"]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.check_call(cmd)
+        os.replace(CLIENT_LIB + ".tmp", CLIENT_LIB)
     return LIB
 
 

@@ -14,7 +14,10 @@
 // requests wait to be grouped into larger ones. A tick's admitted requests are
 // packed into a pinned staging buffer and uploaded with one copy per array and
 // one scatter kernel. Uploads, kernels and downloads run on three streams
-// ordered by events, so copies overlap other requests' kernels. A submission
+// ordered by events, so copies overlap other requests' kernels; a launch
+// group's results are downloaded right behind its kernel, with one copy per
+// result array over the arena range its requests occupy (per request when
+// that range is mostly other requests' space). A submission
 // wakes the scheduler only when it is idle; while work is queued or in
 // flight the scheduler comes back every ~20 us by itself, so a burst of
 // submissions neither waits on a scheduler pass per request nor splits into
@@ -84,7 +87,7 @@ class RangeAlloc {
     std::map<size_t, size_t> free_;
 };
 
-enum class St { QUEUED, ACTIVE, COPYING, DONE, CANCELLED, FAILED };
+enum class St { QUEUED, ACTIVE, DONE, CANCELLED, FAILED };
 
 struct Req {
     uint64_t ticket = 0;
@@ -97,14 +100,21 @@ struct Req {
     bool launched = false;
     int inflight = 0;  // launches referencing this request that have not completed
     double t_submit = 0, t_done = 0;
-    std::vector<double> mjd, t0, chi2;  // inputs until admitted; chi2 = result
-    std::vector<int32_t> band;
-    std::vector<float> flux, fluxerr, zp, z, x0, x1, c, gout;  // gout = gradient result
-    cudaEvent_t ev_down = nullptr;
+    // inputs until admitted, in one buffer: mjd [n_obs], t0 [n_par] (float64),
+    // band, flux, fluxerr, zp [n_obs], z, x0, x1, c [n_par] (32-bit)
+    std::unique_ptr<unsigned char[]> in;
+    std::vector<double> chi2;  // results
+    std::vector<float> gout;
+    const double *mjd() const { return (const double *)in.get(); }
+    const double *t0() const { return mjd() + n_obs; }
+    const int32_t *band() const { return (const int32_t *)(t0() + n_par); }
+    const float *f32(int k) const { return (const float *)(band() + n_obs) + (size_t)k * n_obs; }  // flux, fluxerr, zp
+    const float *par32(int k) const { return f32(3) + (size_t)k * n_par; }                         // z, x0, x1, c
+    static size_t in_bytes(int n, int S) { return 8 * ((size_t)n + S) + 4 * (4 * (size_t)n + 4 * (size_t)S); }
 };
 
 struct Launch {
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;  // the group's results are in the host mirrors
     std::vector<uint64_t> reqs;
     int slot = -1;
 };
@@ -181,10 +191,10 @@ struct ServeEngine {
     std::deque<uint64_t> queue;
     // requests by state, so a tick touches only what can change
     std::vector<uint64_t> pending[2][4];  // admitted, not launched: [chi2 / grad][tile 1, 2, 4, 8]
-    std::vector<uint64_t> copying;        // results on their way to the host
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     std::list<Launch> inflight;
     std::vector<double> lat_ms;
+    std::vector<cudaEvent_t> ev_pool;  // recycled launch events
     uint64_t next_ticket = 1;
     uint64_t n_submitted = 0, n_completed = 0, n_cancelled = 0, n_rejected = 0, n_launches = 0;
     bool stop = false;
@@ -208,8 +218,15 @@ void release_req(ServeEngine *e, Req &r) {
     if (r.oo != SIZE_MAX) e->obs_a.release(r.oo, (size_t)r.n_obs);
     if (r.po != SIZE_MAX) e->par_a.release(r.po, (size_t)r.n_par);
     r.oo = r.po = SIZE_MAX;
-    if (r.ev_down) cudaEventDestroy(r.ev_down);
-    r.ev_down = nullptr;
+}
+
+cudaError_t pool_event(ServeEngine *e, cudaEvent_t *ev) {
+    if (!e->ev_pool.empty()) {
+        *ev = e->ev_pool.back();
+        e->ev_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
 }
 
 // Scatter one tick's staged requests into the arenas: thread per row.
@@ -254,66 +271,78 @@ int tile_for(int n_par) {
 }
 
 template <class T>
-cudaError_t up(T *dst, const std::vector<T> &src, size_t off, cudaStream_t st) {
-    if (src.empty()) return cudaSuccess;
-    return cudaMemcpyAsync(dst + off, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+cudaError_t up(T *dst, const T *src, size_t n, size_t off, cudaStream_t st) {
+    if (!n) return cudaSuccess;
+    return cudaMemcpyAsync(dst + off, src, n * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// Enqueue, on the download stream, the copies of a launch group's results
+// into the host mirrors: one copy per result array over the arena range the
+// group's requests span when that range is at most twice their samples (plus
+// a margin), else one copy per request. Copying other requests' space as well
+// is harmless: a request's results are read from the mirror only after its
+// own group's download, and only its own kernel writes them on the device.
+cudaError_t download_results(ServeEngine *e, const std::vector<uint64_t> &members, bool grad) {
+    size_t lo = SIZE_MAX, hi = 0, need = 0;
+    for (uint64_t t : members) {
+        const Req &r = *e->reqs[t];
+        lo = std::min(lo, r.po);
+        hi = std::max(hi, r.po + (size_t)r.n_par);
+        need += (size_t)r.n_par;
+    }
+    cudaError_t err = cudaSuccess;
+    if (hi > lo && hi - lo <= 2 * need + 4096) {
+        err = cudaMemcpyAsync(e->h_chi2 + lo, e->d_chi2 + lo, 8 * (hi - lo), cudaMemcpyDeviceToHost, e->s_down);
+        if (err == cudaSuccess && grad)
+            err = cudaMemcpyAsync(e->h_grad + 5 * lo, e->d_grad + 5 * lo, 20 * (hi - lo), cudaMemcpyDeviceToHost,
+                                  e->s_down);
+        return err;
+    }
+    for (uint64_t t : members) {
+        const Req &r = *e->reqs[t];
+        err = cudaMemcpyAsync(e->h_chi2 + r.po, e->d_chi2 + r.po, 8 * (size_t)r.n_par, cudaMemcpyDeviceToHost,
+                              e->s_down);
+        if (err == cudaSuccess && grad)
+            err = cudaMemcpyAsync(e->h_grad + 5 * r.po, e->d_grad + 5 * r.po, 20 * (size_t)r.n_par,
+                                  cudaMemcpyDeviceToHost, e->s_down);
+        if (err != cudaSuccess) return err;
+    }
+    return err;
 }
 
 // One scheduler iteration, lock held. Returns false after a CUDA error.
 bool tick(ServeEngine *e) {
     cudaError_t err;
-    // 1. retire finished launches; queue result downloads of finished requests
+    // 1. retire launch groups whose results have reached the host mirrors
+    bool finished = false;
     for (auto it = e->inflight.begin(); it != e->inflight.end();) {
         err = cudaEventQuery(it->ev);
         if (err == cudaErrorNotReady) { ++it; continue; }
         if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
-        for (uint64_t t : it->reqs) {
-            auto rq = e->reqs.find(t);
+        const double t = now_ms();
+        for (uint64_t tk : it->reqs) {
+            auto rq = e->reqs.find(tk);
             if (rq == e->reqs.end()) continue;
             Req &r = *rq->second;
             if (--r.inflight > 0) continue;
-            if (r.cancel) {
-                release_req(e, r);
-                r.st = St::CANCELLED;
-                e->cv_done.notify_all();
-                continue;
+            if (!r.cancel) {
+                r.t_done = t;
+                r.chi2.assign(e->h_chi2 + r.po, e->h_chi2 + r.po + r.n_par);
+                if (r.grad) r.gout.assign(e->h_grad + 5 * r.po, e->h_grad + 5 * (r.po + r.n_par));
             }
-            err = cudaMemcpyAsync(e->h_chi2 + r.po, e->d_chi2 + r.po, 8 * (size_t)r.n_par,
-                                  cudaMemcpyDeviceToHost, e->s_down);
-            if (err == cudaSuccess && r.grad)
-                err = cudaMemcpyAsync(e->h_grad + 5 * r.po, e->d_grad + 5 * r.po, 20 * (size_t)r.n_par,
-                                      cudaMemcpyDeviceToHost, e->s_down);
-            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&r.ev_down, cudaEventDisableTiming);
-            if (err == cudaSuccess) err = cudaEventRecord(r.ev_down, e->s_down);
-            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
-            r.st = St::COPYING;
-            e->copying.push_back(r.ticket);
+            release_req(e, r);
+            r.st = r.cancel ? St::CANCELLED : St::DONE;
+            if (r.st == St::DONE) {
+                e->lat_ms.push_back(r.t_done - r.t_submit);
+                e->n_completed++;
+            }
+            finished = true;
         }
-        cudaEventDestroy(it->ev);
+        e->ev_pool.push_back(it->ev);
         e->slot_busy[it->slot] = false;
         it = e->inflight.erase(it);
     }
-    // 2. finished downloads -> results to the request, release its arena ranges
-    size_t keep = 0;
-    for (size_t qi = 0; qi < e->copying.size(); ++qi) {
-        auto rq = e->reqs.find(e->copying[qi]);
-        if (rq == e->reqs.end() || rq->second->st != St::COPYING) continue;
-        Req &r = *rq->second;
-        err = cudaEventQuery(r.ev_down);
-        if (err == cudaErrorNotReady) { e->copying[keep++] = e->copying[qi]; continue; }
-        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
-        r.t_done = now_ms();
-        r.chi2.assign(e->h_chi2 + r.po, e->h_chi2 + r.po + r.n_par);
-        if (r.grad) r.gout.assign(e->h_grad + 5 * r.po, e->h_grad + 5 * (r.po + r.n_par));
-        release_req(e, r);
-        r.st = r.cancel ? St::CANCELLED : St::DONE;
-        if (r.st == St::DONE) {
-            e->lat_ms.push_back(r.t_done - r.t_submit);
-            e->n_completed++;
-        }
-        e->cv_done.notify_all();
-    }
-    e->copying.resize(keep);
+    if (finished) e->cv_done.notify_all();
     // 3. admit queued requests while both arenas (and the staging buffer) have room (FIFO)
     Stage *sg = nullptr;
     for (int t = 0; t < 2 && !sg; ++t) {
@@ -345,41 +374,39 @@ bool tick(ServeEngine *e) {
         r.po = po;
         if (direct) {
             // pageable sources: each copy is staged by the driver before the call returns
-            err = up(e->d_mjd, r.mjd, oo, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_band, r.band, oo, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_flux, r.flux, oo, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_fluxerr, r.fluxerr, oo, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_zp, r.zp, oo, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_t0, r.t0, po, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_z, r.z, po, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_x0, r.x0, po, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_x1, r.x1, po, e->s_up);
-            if (err == cudaSuccess) err = up(e->d_c, r.c, po, e->s_up);
+            const size_t n = (size_t)r.n_obs, S = (size_t)r.n_par;
+            err = up(e->d_mjd, r.mjd(), n, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_band, r.band(), n, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_flux, r.f32(0), n, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_fluxerr, r.f32(1), n, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_zp, r.f32(2), n, oo, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_t0, r.t0(), S, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_z, r.par32(0), S, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_x0, r.par32(1), S, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_x1, r.par32(2), S, po, e->s_up);
+            if (err == cudaSuccess) err = up(e->d_c, r.par32(3), S, po, e->s_up);
             if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
         } else {
             unsigned char *h = sg->h;
             auto put = [&](size_t base, size_t at, const void *src, size_t bytes) {
                 if (bytes) std::memcpy(h + base + at, src, bytes);
             };
-            put(SL.mjd, 8 * so, r.mjd.data(), 8 * (size_t)r.n_obs);
-            put(SL.band, 4 * so, r.band.data(), 4 * (size_t)r.n_obs);
-            put(SL.flux, 4 * so, r.flux.data(), 4 * (size_t)r.n_obs);
-            put(SL.fluxerr, 4 * so, r.fluxerr.data(), 4 * (size_t)r.n_obs);
-            put(SL.zp, 4 * so, r.zp.data(), 4 * (size_t)r.n_obs);
-            put(SL.t0, 8 * sp, r.t0.data(), 8 * (size_t)r.n_par);
-            put(SL.z, 4 * sp, r.z.data(), 4 * (size_t)r.n_par);
-            put(SL.x0, 4 * sp, r.x0.data(), 4 * (size_t)r.n_par);
-            put(SL.x1, 4 * sp, r.x1.data(), 4 * (size_t)r.n_par);
-            put(SL.c, 4 * sp, r.c.data(), 4 * (size_t)r.n_par);
+            put(SL.mjd, 8 * so, r.mjd(), 8 * (size_t)r.n_obs);
+            put(SL.band, 4 * so, r.band(), 4 * (size_t)r.n_obs);
+            put(SL.flux, 4 * so, r.f32(0), 4 * (size_t)r.n_obs);
+            put(SL.fluxerr, 4 * so, r.f32(1), 4 * (size_t)r.n_obs);
+            put(SL.zp, 4 * so, r.f32(2), 4 * (size_t)r.n_obs);
+            put(SL.t0, 8 * sp, r.t0(), 8 * (size_t)r.n_par);
+            put(SL.z, 4 * sp, r.par32(0), 4 * (size_t)r.n_par);
+            put(SL.x0, 4 * sp, r.par32(1), 4 * (size_t)r.n_par);
+            put(SL.x1, 4 * sp, r.par32(2), 4 * (size_t)r.n_par);
+            put(SL.c, 4 * sp, r.par32(3), 4 * (size_t)r.n_par);
             UpDesc *dsc = (UpDesc *)(h + SL.desc);
             dsc[nd++] = UpDesc{(int64_t)so, (int64_t)oo, r.n_obs, (int64_t)sp, (int64_t)po, r.n_par};
             so += r.n_obs;
             sp += r.n_par;
         }
-        std::vector<double>().swap(r.mjd);
-        std::vector<double>().swap(r.t0);
-        std::vector<int32_t>().swap(r.band);
-        for (auto *v : {&r.flux, &r.fluxerr, &r.zp, &r.z, &r.x0, &r.x1, &r.c}) std::vector<float>().swap(*v);
+        r.in.reset();
         r.st = St::ACTIVE;
         e->pending[r.grad ? 1 : 0][r.tile == 1 ? 0 : r.tile == 2 ? 1 : r.tile == 4 ? 2 : 3].push_back(r.ticket);
         uploaded = true;
@@ -463,8 +490,11 @@ bool tick(ServeEngine *e) {
             if (err == cudaSuccess)
                 err = launch_factorised_items(e->ctx, tile, e->items_d[slot], n_items, e->counters_d + 4 * slot,
                                               b, o, mode, e->s_comp);
-            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+            if (err == cudaSuccess) err = pool_event(e, &L.ev);
             if (err == cudaSuccess) err = cudaEventRecord(L.ev, e->s_comp);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(e->s_down, L.ev, 0);
+            if (err == cudaSuccess) err = download_results(e, members, mode == MODE_GRAD);
+            if (err == cudaSuccess) err = cudaEventRecord(L.ev, e->s_down);
             if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
             e->slot_busy[slot] = true;
             e->n_launches++;
@@ -480,7 +510,7 @@ bool tick(ServeEngine *e) {
 }
 
 bool has_work(ServeEngine *e) {
-    if (!e->inflight.empty() || !e->queue.empty() || !e->copying.empty()) return true;
+    if (!e->inflight.empty() || !e->queue.empty()) return true;
     for (auto &mode : e->pending)
         for (auto &bucket : mode)
             if (!bucket.empty()) return true;
@@ -568,8 +598,7 @@ void serve_destroy(ServeEngine *e) {
         if (s) cudaStreamSynchronize(s);
     for (auto &L : e->inflight)
         if (L.ev) cudaEventDestroy(L.ev);
-    for (auto &kv : e->reqs)
-        if (kv.second->ev_down) cudaEventDestroy(kv.second->ev_down);
+    for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
     for (int q = 0; q < kSlots; ++q) {
         if (e->items_d[q]) cudaFree(e->items_d[q]);
         if (e->items_h[q]) cudaFreeHost(e->items_h[q]);
@@ -615,16 +644,25 @@ int serve_submit(ServeEngine *e, const salt_request *q, uint64_t *ticket) {
     r->n_par = S;
     r->grad = q->want_grad != 0;
     r->tile = tile_for(S);
-    r->mjd.assign(q->mjd, q->mjd + n);
-    r->band.assign(q->band, q->band + n);
-    r->flux.assign(q->flux, q->flux + n);
-    r->fluxerr.assign(q->fluxerr, q->fluxerr + n);
-    r->zp.assign(q->zp, q->zp + n);
-    r->t0.assign(q->t0, q->t0 + S);
-    r->z.assign(q->z, q->z + S);
-    r->x0.assign(q->x0, q->x0 + S);
-    r->x1.assign(q->x1, q->x1 + S);
-    r->c.assign(q->c, q->c + S);
+    r->in.reset(new (std::nothrow) unsigned char[Req::in_bytes(n, S)]);
+    if (!r->in) return SALT_ERR_OOM;
+    {
+        unsigned char *p = r->in.get();
+        auto put = [&p](const void *src, size_t bytes) {
+            if (bytes) std::memcpy(p, src, bytes);
+            p += bytes;
+        };
+        put(q->mjd, 8 * (size_t)n);
+        put(q->t0, 8 * (size_t)S);
+        put(q->band, 4 * (size_t)n);
+        put(q->flux, 4 * (size_t)n);
+        put(q->fluxerr, 4 * (size_t)n);
+        put(q->zp, 4 * (size_t)n);
+        put(q->z, 4 * (size_t)S);
+        put(q->x0, 4 * (size_t)S);
+        put(q->x1, 4 * (size_t)S);
+        put(q->c, 4 * (size_t)S);
+    }
     r->t_submit = now_ms();
     bool wake = false;
     {
@@ -699,7 +737,7 @@ int serve_stats(ServeEngine *e, salt_serve_stats *out) {
     out->queued = e->queue.size();
     uint64_t act = 0;
     for (auto &kv : e->reqs)
-        if (kv.second->st == St::ACTIVE || kv.second->st == St::COPYING) act++;
+        if (kv.second->st == St::ACTIVE) act++;
     out->active = act;
     out->mem_in_use = e->obs_a.used() * kObsBytes + e->par_a.used() * kParBytes;
     out->mem_limit = e->obs_a.size() * kObsBytes + e->par_a.size() * kParBytes;

@@ -98,6 +98,61 @@ def replay(salt: Salt, requests, arrivals_s=None, collect=True):
     return wall, results, salt.serve_stats()
 
 
+def _request_array(prep):
+    """ctypes array of salt_request descriptors (the prepared entries keep the
+    host arrays alive)."""
+    arr = (_abi.Request * max(1, len(prep)))()
+    for i, p in enumerate(prep):
+        arr[i] = p[0]
+    return arr
+
+
+def replay_native(salt: Salt, requests, arrivals_s=None, collect=False):
+    """The replay of `replay` from the native client (salt_client_replay): a
+    submitting and a polling thread in C++, no interpreter in the loop.
+    Returns (wall seconds, results list or None, engine stats dict, client
+    stats dict)."""
+    import ctypes as C
+    n = len(requests)
+    prep = _prepared(requests)
+    reqs = _request_array(prep)
+    arr = None if arrivals_s is None else np.ascontiguousarray(arrivals_s, np.float64)
+    c_out = g_out = None
+    if collect:
+        c_out = (C.c_void_p * n)(*[p[2].ctypes.data for p in prep])
+        g_out = (C.c_void_p * n)(*[p[3].ctypes.data if p[3] is not None else None for p in prep])
+    lat = np.zeros(n)
+    st = _abi.ReplayStats()
+    rc = _abi.client().salt_client_replay(salt.ctx.h, C.addressof(reqs), n,
+                                          None if arr is None else arr.ctypes.data,
+                                          None if c_out is None else C.addressof(c_out),
+                                          None if g_out is None else C.addressof(g_out), lat.ctypes.data,
+                                          C.byref(st))
+    if rc != _abi.SALT_OK:
+        raise _abi.SaltError(rc, "replay")
+    results = [(p[2], p[3]) for p in prep] if collect else None
+    cs = {"wall_s": st.wall_s, "submit_s": st.submit_s, "completed": int(st.completed),
+          "client_p50_ms": st.p50_ms, "client_p99_ms": st.p99_ms}
+    return st.wall_s, results, salt.serve_stats(), cs
+
+
+def plain_native(salt: Salt, requests, limit_s: float = 8.0, pack_bytes: int = 1 << 30):
+    """The same requests as plain per-request batch calls from the native
+    client (salt_client_plain): inputs pre-packed in pinned memory, per request
+    one upload into preallocated device buffers, one plan-less salt_chi2 /
+    salt_chi2_grad, one download, a synchronisation. Returns (requests done,
+    wall seconds, p50 ms, p99 ms)."""
+    import ctypes as C
+    prep = _prepared(requests)
+    reqs = _request_array(prep)
+    st = _abi.PlainStats()
+    rc = _abi.client().salt_client_plain(salt.ctx.h, C.addressof(reqs), len(prep), limit_s, pack_bytes, None,
+                                         C.byref(st))
+    if rc != _abi.SALT_OK:
+        raise _abi.SaltError(rc, "plain")
+    return int(st.completed), st.wall_s, st.p50_ms, st.p99_ms
+
+
 def plain_per_request(salt: Salt, requests, limit_s: float = 20.0):
     """Each request alone: its own upload, one launch, result download, sync.
     Returns (requests done, wall seconds, per-request latency ms)."""
@@ -123,21 +178,27 @@ def plain_per_request(salt: Salt, requests, limit_s: float = 20.0):
 
 def run_serving_bench(device: int = 0, n_req: int = 20000, seed: int = 1004,
                       rates=(0.5, 0.8, 0.95), serve_mem: int = 512 << 20, max_replay_s: float = 8.0):
-    """Saturated throughput, Poisson replays at fractions of it, and the
-    plain per-request baseline on the same request stream."""
+    """Saturated throughput, Poisson replays at fractions of it, and the plain
+    per-request baseline on the same request stream, all driven by the native
+    client (salt_client.h); beside them the device time of the same requests
+    as two batch calls."""
     import workloads as W
     wl = W.config4(seed=seed, n_req=n_req)
     reqs = wl.requests
     out = {"requests": len(reqs),
            "samples_total": int(sum(r.batch.n_par for r in reqs)),
-           "bandfluxes_total": int(sum(r.batch.n_par * r.batch.n_obs for r in reqs))}
+           "bandfluxes_total": int(sum(r.batch.n_par * r.batch.n_obs for r in reqs)),
+           "client": "native (salt_client_replay / salt_client_plain: C++ threads over the C ABI)"}
     # saturated: everything submitted at once
     s = Salt(wl.model, wl.bands, device=device, serve_mem_bytes=serve_mem)
-    wall, _, st = replay(s, reqs, None, collect=False)
+    replay_native(s, reqs[:500])  # warm the engine (first launches, allocator)
+    s.close()
+    s = Salt(wl.model, wl.bands, device=device, serve_mem_bytes=serve_mem)
+    wall, _, st, cs = replay_native(s, reqs)
     sat = len(reqs) / wall
     out["saturated"] = {"req_per_s": sat, "bandfluxes_per_s": out["bandfluxes_total"] / wall,
                         "wall_s": wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                        "launches": st["launches"]}
+                        "launches": st["launches"], **cs}
     s.close()
     rng = np.random.default_rng(seed + 1)
     for fr in rates:
@@ -145,10 +206,10 @@ def run_serving_bench(device: int = 0, n_req: int = 20000, seed: int = 1004,
         n = int(min(len(reqs), max(200, rate * max_replay_s)))
         arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
         s = Salt(wl.model, wl.bands, device=device, serve_mem_bytes=serve_mem)
-        wall, _, st = replay(s, reqs[:n], arr, collect=False)
+        wall, _, st, cs = replay_native(s, reqs[:n], arr)
         out[f"poisson_{fr:.2f}"] = {"offered_req_per_s": rate, "served_req_per_s": n / wall,
                                      "requests": n, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                                     "launches": st["launches"]}
+                                     "launches": st["launches"], **cs}
         s.close()
     # the same requests as two batch calls (the chi^2-only ones, the gradient
     # ones): the device time the stream needs without any serving machinery
@@ -177,10 +238,12 @@ def run_serving_bench(device: int = 0, n_req: int = 20000, seed: int = 1004,
     s.close()
     # plain per-request launches on the same stream (closed loop, bounded time)
     s = Salt(wl.model, wl.bands, device=device)
-    k, wall, lat = plain_per_request(s, reqs, limit_s=max_replay_s)
-    out["plain_per_request"] = {"req_per_s": k / wall, "requests": k,
-                                "p50_ms": float(np.percentile(lat, 50)),
-                                "p99_ms": float(np.percentile(lat, 99))}
+    plain_native(s, reqs[:50], limit_s=1.0)  # warm
+    k, wall, p50, p99 = plain_native(s, reqs, limit_s=max_replay_s)
+    out["plain_per_request"] = {"req_per_s": k / wall, "requests": k, "p50_ms": p50, "p99_ms": p99,
+                                "how": "native loop over the C ABI: per request one upload from pinned "
+                                       "memory into preallocated device buffers, a plan-less salt_chi2 / "
+                                       "salt_chi2_grad, one download, a synchronisation"}
     out["batched_vs_plain_throughput"] = sat / (k / wall)
     s.close()
     return out

@@ -12,9 +12,9 @@ HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.j
            if f.endswith(".h")]
 
 
-def declared_symbols():
+def declared_symbols(headers=None):
     names = set()
-    for h in HEADERS:
+    for h in (HEADERS if headers is None else headers):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(salt_\w+)\s*\(", text, flags=re.M):
@@ -39,10 +39,16 @@ def test_header_declares_the_boundary():
 
 def test_every_declared_symbol_is_exported(lib):
     from paper_2504_08081_b300 import _abi
-    names = declared_symbols()
+    names = declared_symbols([os.path.join(ROOT, "include", "salt.h")])
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
     assert names == set(_abi.EXPORTS), names ^ set(_abi.EXPORTS)
+    # the native client library exports what salt_client.h declares
+    client = _abi.client()
+    cnames = declared_symbols([os.path.join(ROOT, "include", "salt_client.h")])
+    assert cnames == set(_abi.CLIENT_EXPORTS), cnames ^ set(_abi.CLIENT_EXPORTS)
+    assert all(hasattr(client, n) for n in cnames)
+    assert declared_symbols() == names | cnames  # no other header declares entry points
 
 
 def test_host_helpers_without_gpu(lib):
@@ -62,3 +68,8 @@ def test_host_helpers_without_gpu(lib):
     assert lib.salt_serve_submit(None, None, None) == _abi.SALT_ERR_INVALID
     h = C.c_void_p()
     assert lib.salt_init_model(None, None, 0, 0, 0, C.byref(h)) == _abi.SALT_ERR_INVALID
+    st = _abi.ReplayStats()
+    assert _abi.client().salt_client_replay(None, None, 0, None, None, None, None, C.byref(st)) == \
+        _abi.SALT_ERR_INVALID
+    ps = _abi.PlainStats()
+    assert _abi.client().salt_client_plain(None, None, 0, 1.0, 0, None, C.byref(ps)) == _abi.SALT_ERR_INVALID

@@ -168,3 +168,26 @@ def test_burst_with_cancels_accounts_for_every_request():
             scale = np.abs(ref).max(axis=1, keepdims=True)
             assert np.all(np.abs(prep[i][3] - ref) <= 1e-5 * scale)
     s.close()
+
+
+def test_native_client_replay_and_plain(stream):
+    """The native load generator (salt_client.h): a replay submitted all at
+    once and one on Poisson arrivals give bitwise the results the engine gives
+    through the Python client, every request completes, and the plain
+    per-request loop over the C ABI runs the same requests."""
+    from paper_2504_08081_b300 import serving as SV
+    reqs = stream.requests
+    s = _salt(stream, serve_mem_bytes=256 << 20)
+    ref = {}
+    for i in (0, 7, 33, 119):
+        ref[i] = _result(s, _submit(s, reqs[i]), reqs[i])
+    for arrivals in (None, np.cumsum(np.random.default_rng(5).exponential(1e-4, len(reqs)))):
+        wall, res, st, cs = SV.replay_native(s, reqs, arrivals, collect=True)
+        assert cs["completed"] == len(reqs) and wall > 0 and cs["client_p99_ms"] >= cs["client_p50_ms"] > 0
+        for i, (x2, g) in ref.items():
+            np.testing.assert_array_equal(res[i][0], x2)
+            if reqs[i].want_grad:
+                np.testing.assert_array_equal(res[i][1], g)
+    k, wall, p50, p99 = SV.plain_native(s, reqs, limit_s=30.0)
+    assert k == len(reqs) and p99 >= p50 > 0
+    s.close()
