@@ -63,7 +63,7 @@ struct Lay {
         Q = o;       o = al16(o + (grad ? 4 * (size_t)THREADS * tj : 0));
         D = o;       o = al16(o + 4 * (size_t)n_phase * tj * 2);
         Yw = o;      o = al16(o + (grad ? 4 * (size_t)nslot * n_phase : 0));
-        kst = o;     o = al16(o + 4 * (size_t)WARPS * 64);
+        kst = o;     o = al16(o + 4 * (size_t)WARPS * 128);
         red = o;     o = al16(o + 8 * (size_t)nslot * 8);
         total = o;
     }
@@ -167,7 +167,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     double *sMjd = (double *)(smem + L.mjd);
     int *sBand = (int *)(smem + L.band);
     float *sFlux = (float *)(smem + L.flux);
-    float *sSig = (float *)(smem + L.sig);
+    float *sSig = (float *)(smem + L.sig);  // 1 / fluxerr
     double *sRed = (double *)(smem + L.red);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -175,7 +175,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     const int NW = m.n_wave;
     const int NP = m.n_phase;
     // per-warp staging for the column-response build and the adjoint scatter
-    float *yval = (float *)(smem + L.kst) + warp * 64;  // per-warp adjoint scatter staging
+    float *yval = (float *)(smem + L.kst) + warp * 128;  // per-warp adjoint scatter staging (32 float4)
     // every band's samples stay in shared memory for the CTA's lifetime
     const bool bands_staged = TJ <= 8 && m.bands.k_total <= KTOT;
     if (bands_staged)
@@ -261,7 +261,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     sBand[i] = (okb && e > 0.f) ? bd : -1;
                     sMjd[i] = b.mjd[obase + i];
                     sFlux[i] = b.flux[obase + i];
-                    sSig[i] = e;
+                    sSig[i] = 1.0f / e;  // 1/sigma (never used when e <= 0: band id -1)
                 }
                 __syncthreads();
                 if (warp == 0) {
@@ -387,8 +387,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     const int nrows = sMisc[6];
                     const int C_lo = sMisc[4], C_hi = sMisc[5];
                     for (int q = tid; q < nrows * TJ * 2; q += THREADS) {
-                        const int rr = q / (TJ * 2);
-                        sD[sRows[rr] * TJ * 2 + (q - rr * TJ * 2)] = 0.f;
+                        const int rr = q / (TJ * 2), jj2 = q - rr * TJ * 2;  // (sample, surface)
+                        sD[((jj2 >> 1) * NP + sRows[rr]) * 2 + (jj2 & 1)] = 0.f;
                     }
                     const int n_cchunks = (C_hi >= C_lo) ? (C_hi - C_lo + WMAX) / WMAX : 0;
                     // ---- 2. column response + forward GEMM, per column chunk
@@ -447,8 +447,11 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 if (valid && l4 == 0) {
 #pragma unroll
                                     for (int j = 0; j < TJ; ++j) {
-                                        sD[(r * TJ + j) * 2] += acc0[j];
-                                        sD[(r * TJ + j) * 2 + 1] += acc1[j];
+                                        float2 *dv = reinterpret_cast<float2 *>(sD + (j * NP + r) * 2);
+                                        float2 d = *dv;
+                                        d.x += acc0[j];
+                                        d.y += acc1[j];
+                                        *dv = d;
                                     }
                                 }
                             }
@@ -480,7 +483,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                         axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                                         for (int mm = 0; mm < 4; ++mm) {
-                                            const float2 dv = *reinterpret_cast<const float2 *>(sD + ((tp.first + mm) * TJ + j) * 2);
+                                            const float2 dv = *reinterpret_cast<const float2 *>(sD + (j * NP + tp.first + mm) * 2);
                                             const float h = fmaf(x1, dv.y, dv.x);
                                             Bs = fmaf(tp.w[mm], h, Bs);
                                             if (GRAD) {
@@ -498,11 +501,11 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     if (MODE == MODE_BANDFLUX) {
                                         o.bandflux[wi.bf0 + (int64_t)(jloc0 + j) * nobs + (oc + i)] = B;
                                     } else {
-                                        const float sig = sSig[i];
-                                        const float r = (sFlux[i] - B) / sig;
+                                        const float isig = sSig[i];
+                                        const float r = (sFlux[i] - B) * isig;
                                         chi_acc[jj] = fma((double)r, (double)r, chi_acc[jj]);
                                         if (GRAD) {
-                                            const float g = -2.0f * r / sig;
+                                            const float g = -2.0f * r * isig;
                                             gacc[jj][0] += g * (-a * B - pre * a * p * Bp);
                                             gacc[jj][1] += g * pre * Bp * (-a);
                                             gacc[jj][2] += g * a * zpf * Bs;
@@ -512,25 +515,38 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     }
                                 }
                                 if (GRAD) {
-                                    // Y[r] += coef * phi_m for the 4 taps; lanes sharing a row are
-                                    // summed by the lowest lane in lane order (deterministic)
-#pragma unroll
-                                    for (int mm = 0; mm < 4; ++mm) {
-                                        const bool has = tp.first >= 0;
-                                        const int key = has ? tp.first + mm : -1 - lane;
-                                        yval[lane] = has ? coef * tp.w[mm] : 0.f;
+                                    // Y[first + m] += coef * phi_m for the 4 taps. Lanes with the
+                                    // same first row form one group for all 4 taps; each group's
+                                    // sums run in lane order (deterministic) and its lowest lane
+                                    // adds them, tap by tap, so groups whose rows overlap add in
+                                    // a fixed order too.
+                                    const bool has = tp.first >= 0;
+                                    const int key = has ? tp.first : -1 - lane;
+                                    float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
+                                    if (has)
+                                        yv = make_float4(coef * tp.w[0], coef * tp.w[1], coef * tp.w[2],
+                                                         coef * tp.w[3]);
+                                    const unsigned grp = __match_any_sync(0xffffffffu, key);
+                                    const bool lead = has && lane == __ffs(grp) - 1;
+                                    if (!__all_sync(0xffffffffu, grp == (1u << lane))) {
+                                        reinterpret_cast<float4 *>(yval)[lane] = yv;
                                         __syncwarp();
-                                        const unsigned grp = __match_any_sync(0xffffffffu, key);
-                                        if (has && lane == __ffs(grp) - 1) {
-                                            float s = 0.f;
+                                        if (lead) {
+                                            float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
                                             unsigned g2 = grp;
                                             while (g2) {
-                                                const int src = __ffs(g2) - 1;
-                                                s += yval[src];
+                                                const float4 v = reinterpret_cast<const float4 *>(yval)[__ffs(g2) - 1];
+                                                s4.x += v.x; s4.y += v.y; s4.z += v.z; s4.w += v.w;
                                                 g2 &= g2 - 1;
                                             }
-                                            yw[key] += s;
+                                            yv = s4;
                                         }
+                                        __syncwarp();
+                                    }
+                                    const float ys[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+                                    for (int mm = 0; mm < 4; ++mm) {
+                                        if (lead) yw[key + mm] += ys[mm];
                                         __syncwarp();
                                     }
                                 }
