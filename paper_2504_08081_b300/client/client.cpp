@@ -92,23 +92,39 @@ extern "C" int salt_client_replay(salt_ctx *ctx, const salt_request *reqs, int32
         t_sub_end = Clock::now();
     });
 
+    // The poller sweeps, without waiting, the oldest outstanding requests (a
+    // window of kWin), so a request's completion time is taken when its own
+    // results are ready, not after the slower requests submitted before it.
+    constexpr int kWin = 32;
     std::vector<double> chi2_tmp((size_t)max_par);
     std::vector<float> grad_tmp(5 * (size_t)max_par);
+    std::vector<char> fin((size_t)n, 0);
     int64_t done = 0;
-    for (int i = 0; i < n; ++i) {
-        int st;
-        while ((st = state[(size_t)i].load(std::memory_order_acquire)) == 0) std::this_thread::yield();
-        if (st == 2) continue;
-        double *c2 = (chi2_out && chi2_out[i]) ? chi2_out[i] : chi2_tmp.data();
-        float *g = (grad_out && grad_out[i]) ? grad_out[i] : grad_tmp.data();
-        const int rc = salt_serve_poll(ctx, tickets[(size_t)i], -1, c2, reqs[i].want_grad ? g : nullptr);
-        t_done[(size_t)i] = Clock::now();
-        if (rc == SALT_OK) {
-            ++done;
-        } else {
-            int expect = SALT_OK;
-            first_err.compare_exchange_strong(expect, rc);
+    int head = 0;  // every request before head is finished
+    while (head < n) {
+        bool progress = false;
+        const int end = std::min(n, head + kWin);
+        for (int i = head; i < end; ++i) {
+            if (fin[(size_t)i]) continue;
+            const int st = state[(size_t)i].load(std::memory_order_acquire);
+            if (st == 0) break;  // not submitted yet: neither are the later ones
+            if (st == 2) { fin[(size_t)i] = 1; progress = true; continue; }
+            double *c2 = (chi2_out && chi2_out[i]) ? chi2_out[i] : chi2_tmp.data();
+            float *g = (grad_out && grad_out[i]) ? grad_out[i] : grad_tmp.data();
+            const int rc = salt_serve_poll(ctx, tickets[(size_t)i], 0, c2, reqs[i].want_grad ? g : nullptr);
+            if (rc == SALT_PENDING) continue;
+            t_done[(size_t)i] = Clock::now();
+            fin[(size_t)i] = 1;
+            progress = true;
+            if (rc == SALT_OK) {
+                ++done;
+            } else {
+                int expect = SALT_OK;
+                first_err.compare_exchange_strong(expect, rc);
+            }
         }
+        while (head < n && fin[(size_t)head]) ++head;
+        if (!progress) std::this_thread::yield();
     }
     submitter.join();
     const Clock::time_point t_end = Clock::now();

@@ -87,7 +87,9 @@ class RangeAlloc {
     std::map<size_t, size_t> free_;
 };
 
-enum class St { QUEUED, ACTIVE, DONE, CANCELLED, FAILED };
+// ADMITTING: arena ranges taken, inputs being packed and uploaded by the scheduler
+// outside the engine lock (poll and cancel only flag it)
+enum class St { QUEUED, ADMITTING, ACTIVE, DONE, CANCELLED, FAILED };
 
 struct Req {
     uint64_t ticket = 0;
@@ -282,10 +284,10 @@ cudaError_t up(T *dst, const T *src, size_t n, size_t off, cudaStream_t st) {
 // a margin), else one copy per request. Copying other requests' space as well
 // is harmless: a request's results are read from the mirror only after its
 // own group's download, and only its own kernel writes them on the device.
-cudaError_t download_results(ServeEngine *e, const std::vector<uint64_t> &members, bool grad) {
+cudaError_t download_results(ServeEngine *e, const std::vector<Req *> &members, bool grad) {
     size_t lo = SIZE_MAX, hi = 0, need = 0;
-    for (uint64_t t : members) {
-        const Req &r = *e->reqs[t];
+    for (const Req *rp : members) {
+        const Req &r = *rp;
         lo = std::min(lo, r.po);
         hi = std::max(hi, r.po + (size_t)r.n_par);
         need += (size_t)r.n_par;
@@ -298,8 +300,8 @@ cudaError_t download_results(ServeEngine *e, const std::vector<uint64_t> &member
                                   e->s_down);
         return err;
     }
-    for (uint64_t t : members) {
-        const Req &r = *e->reqs[t];
+    for (const Req *rp : members) {
+        const Req &r = *rp;
         err = cudaMemcpyAsync(e->h_chi2 + r.po, e->d_chi2 + r.po, 8 * (size_t)r.n_par, cudaMemcpyDeviceToHost,
                               e->s_down);
         if (err == cudaSuccess && grad)
@@ -310,8 +312,16 @@ cudaError_t download_results(ServeEngine *e, const std::vector<uint64_t> &member
     return err;
 }
 
-// One scheduler iteration, lock held. Returns false after a CUDA error.
-bool tick(ServeEngine *e) {
+// One scheduler pass, entered and left with the engine lock held. Under the
+// lock it retires finished launch groups, takes arena ranges for the queued
+// requests that fit (FIFO; they become ADMITTING) and picks the launch groups;
+// it then releases the lock while it packs and uploads the admitted requests
+// and builds and launches the groups (submit, poll and cancel go on meanwhile:
+// the requests it works on are ADMITTING or already marked launched, which
+// poll and cancel only flag, and it reaches them through their own pointers,
+// never through the request map), and commits under the lock again. Returns
+// false after a CUDA error.
+bool tick(ServeEngine *e, std::unique_lock<std::mutex> &lk) {
     cudaError_t err;
     // 1. retire launch groups whose results have reached the host mirrors
     bool finished = false;
@@ -343,7 +353,9 @@ bool tick(ServeEngine *e) {
         it = e->inflight.erase(it);
     }
     if (finished) e->cv_done.notify_all();
-    // 3. admit queued requests while both arenas (and the staging buffer) have room (FIFO)
+
+    // 2. admission: arena ranges for the queued requests while both arenas (and
+    // the staging buffer) have room, FIFO
     Stage *sg = nullptr;
     for (int t = 0; t < 2 && !sg; ++t) {
         Stage &c = e->stage[(e->stage_cur + t) & 1];
@@ -356,10 +368,14 @@ bool tick(ServeEngine *e) {
         sg = &c;
         e->stage_cur = (e->stage_cur + t) & 1;
     }
-    const StageLayout &SL = e->SL;
-    size_t so = 0, sp = 0;  // staged observations / samples this tick
+    struct Adm {
+        Req *r;
+        size_t so, sp;  // rows in the staging buffer (not used for direct uploads)
+        bool direct;
+    };
+    std::vector<Adm> adm;
+    size_t so = 0, sp = 0;  // staged observations / samples this pass
     int nd = 0;
-    bool uploaded = false;
     while (!e->queue.empty()) {
         auto rq = e->reqs.find(e->queue.front());
         if (rq == e->reqs.end() || rq->second->st != St::QUEUED) { e->queue.pop_front(); continue; }
@@ -372,9 +388,78 @@ bool tick(ServeEngine *e) {
         if (!e->obs_a.alloc((size_t)r.n_obs, oo)) { e->par_a.release(po, (size_t)r.n_par); break; }
         r.oo = oo;
         r.po = po;
-        if (direct) {
+        adm.push_back(Adm{&r, so, sp, direct});
+        if (!direct) {
+            so += r.n_obs;
+            sp += r.n_par;
+            ++nd;
+        }
+        r.st = St::ADMITTING;
+        e->pending[r.grad ? 1 : 0][r.tile == 1 ? 0 : r.tile == 2 ? 1 : r.tile == 4 ? 2 : 3].push_back(r.ticket);
+        e->queue.pop_front();
+    }
+
+    // 3. launch groups: one per (mode, tile) over the requests admitted and not
+    // yet launched (this pass's included: their uploads come first in stream
+    // order); while enough launches keep the GPU busy, requests gather into
+    // larger groups
+    const int chunk = std::max(1, e->ctx->serve_chunk);
+    struct Grp {
+        int mode, tile, slot;
+        std::vector<Req *> members;
+        std::vector<uint64_t> tickets;
+        cudaEvent_t ev;
+    };
+    std::vector<Grp> grps;
+    for (int mode = MODE_CHI2; mode <= MODE_GRAD; ++mode) {
+        for (int ti = 0; ti < 4; ++ti) {
+            std::vector<uint64_t> &bucket = e->pending[mode == MODE_GRAD ? 1 : 0][ti];
+            if (bucket.empty()) continue;
+            if ((int)(e->inflight.size() + grps.size()) >= e->max_inflight) break;
+            int slot = -1;
+            for (int q = 0; q < kSlots; ++q)
+                if (!e->slot_busy[q]) { slot = q; break; }
+            if (slot < 0) break;  // all item buffers in flight: next pass
+            Grp G{mode, 1 << ti, slot, {}, {}, nullptr};
+            std::vector<uint64_t> later;
+            int n_items = 0;
+            for (uint64_t t : bucket) {
+                auto rq = e->reqs.find(t);
+                if (rq == e->reqs.end()) continue;
+                Req &r = *rq->second;
+                if ((r.st != St::ACTIVE && r.st != St::ADMITTING) || r.launched || r.cancel) continue;
+                // a request too large for one item list takes larger chunks
+                const int cr = std::max(chunk, (r.n_par + kMaxItems - 1) / kMaxItems);
+                const int need = (r.n_par + cr - 1) / cr;
+                if (n_items + need > kMaxItems) { later.push_back(t); continue; }
+                n_items += need;
+                r.launched = true;
+                r.inflight = 1;
+                G.members.push_back(&r);
+                G.tickets.push_back(t);
+            }
+            bucket.swap(later);
+            if (G.members.empty()) continue;
+            err = pool_event(e, &G.ev);
+            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
+            e->slot_busy[slot] = true;
+            grps.push_back(std::move(G));
+        }
+    }
+    if (adm.empty() && grps.empty()) return true;
+
+    // 4. outside the lock: pack and upload the admitted requests, build and
+    // launch the groups, and queue their result downloads
+    Stage *sgu = nd > 0 ? sg : nullptr;
+    lk.unlock();
+    err = cudaSuccess;
+    const StageLayout &SL = e->SL;
+    for (const Adm &ad : adm) {
+        if (err != cudaSuccess) break;
+        const Req &r = *ad.r;
+        const size_t n = (size_t)r.n_obs, S = (size_t)r.n_par, oo = r.oo, po = r.po;
+        if (ad.direct) {
             // pageable sources: each copy is staged by the driver before the call returns
-            const size_t n = (size_t)r.n_obs, S = (size_t)r.n_par;
             err = up(e->d_mjd, r.mjd(), n, oo, e->s_up);
             if (err == cudaSuccess) err = up(e->d_band, r.band(), n, oo, e->s_up);
             if (err == cudaSuccess) err = up(e->d_flux, r.f32(0), n, oo, e->s_up);
@@ -385,127 +470,111 @@ bool tick(ServeEngine *e) {
             if (err == cudaSuccess) err = up(e->d_x0, r.par32(1), S, po, e->s_up);
             if (err == cudaSuccess) err = up(e->d_x1, r.par32(2), S, po, e->s_up);
             if (err == cudaSuccess) err = up(e->d_c, r.par32(3), S, po, e->s_up);
-            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
         } else {
-            unsigned char *h = sg->h;
+            unsigned char *h = sgu->h;
             auto put = [&](size_t base, size_t at, const void *src, size_t bytes) {
                 if (bytes) std::memcpy(h + base + at, src, bytes);
             };
-            put(SL.mjd, 8 * so, r.mjd(), 8 * (size_t)r.n_obs);
-            put(SL.band, 4 * so, r.band(), 4 * (size_t)r.n_obs);
-            put(SL.flux, 4 * so, r.f32(0), 4 * (size_t)r.n_obs);
-            put(SL.fluxerr, 4 * so, r.f32(1), 4 * (size_t)r.n_obs);
-            put(SL.zp, 4 * so, r.f32(2), 4 * (size_t)r.n_obs);
-            put(SL.t0, 8 * sp, r.t0(), 8 * (size_t)r.n_par);
-            put(SL.z, 4 * sp, r.par32(0), 4 * (size_t)r.n_par);
-            put(SL.x0, 4 * sp, r.par32(1), 4 * (size_t)r.n_par);
-            put(SL.x1, 4 * sp, r.par32(2), 4 * (size_t)r.n_par);
-            put(SL.c, 4 * sp, r.par32(3), 4 * (size_t)r.n_par);
-            UpDesc *dsc = (UpDesc *)(h + SL.desc);
-            dsc[nd++] = UpDesc{(int64_t)so, (int64_t)oo, r.n_obs, (int64_t)sp, (int64_t)po, r.n_par};
-            so += r.n_obs;
-            sp += r.n_par;
+            put(SL.mjd, 8 * ad.so, r.mjd(), 8 * n);
+            put(SL.band, 4 * ad.so, r.band(), 4 * n);
+            put(SL.flux, 4 * ad.so, r.f32(0), 4 * n);
+            put(SL.fluxerr, 4 * ad.so, r.f32(1), 4 * n);
+            put(SL.zp, 4 * ad.so, r.f32(2), 4 * n);
+            put(SL.t0, 8 * ad.sp, r.t0(), 8 * S);
+            put(SL.z, 4 * ad.sp, r.par32(0), 4 * S);
+            put(SL.x0, 4 * ad.sp, r.par32(1), 4 * S);
+            put(SL.x1, 4 * ad.sp, r.par32(2), 4 * S);
+            put(SL.c, 4 * ad.sp, r.par32(3), 4 * S);
         }
-        r.in.reset();
-        r.st = St::ACTIVE;
-        e->pending[r.grad ? 1 : 0][r.tile == 1 ? 0 : r.tile == 2 ? 1 : r.tile == 4 ? 2 : 3].push_back(r.ticket);
-        uploaded = true;
-        e->queue.pop_front();
     }
-    if (nd > 0) {
-        // one transfer per array (used prefix) and one scatter kernel for the whole tick
+    if (err == cudaSuccess && sgu) {
+        UpDesc *dsc = (UpDesc *)(sgu->h + SL.desc);
+        int q = 0;
+        for (const Adm &ad : adm)
+            if (!ad.direct)
+                dsc[q++] = UpDesc{(int64_t)ad.so, (int64_t)ad.r->oo, ad.r->n_obs, (int64_t)ad.sp, (int64_t)ad.r->po,
+                                  ad.r->n_par};
+        // one transfer per array (used prefix) and one scatter kernel for the whole pass
         const size_t parts[][2] = {{SL.mjd, 8 * so}, {SL.band, 4 * so}, {SL.flux, 4 * so},
                                    {SL.fluxerr, 4 * so}, {SL.zp, 4 * so}, {SL.t0, 8 * sp},
                                    {SL.z, 4 * sp}, {SL.x0, 4 * sp}, {SL.x1, 4 * sp},
                                    {SL.c, 4 * sp}, {SL.desc, sizeof(UpDesc) * (size_t)nd}};
-        err = cudaSuccess;
         for (const auto &pt : parts)
             if (err == cudaSuccess && pt[1])
-                err = cudaMemcpyAsync(sg->d + pt[0], sg->h + pt[0], pt[1], cudaMemcpyHostToDevice, e->s_up);
+                err = cudaMemcpyAsync(sgu->d + pt[0], sgu->h + pt[0], pt[1], cudaMemcpyHostToDevice, e->s_up);
         if (err == cudaSuccess) {
             const int64_t rows = (int64_t)std::max(so, sp);
             const int blocks = (int)std::min<int64_t>((rows + 255) / 256, 4 * (int64_t)e->ctx->num_sms);
             k_stage_scatter<<<std::max(blocks, 1), 256, 0, e->s_up>>>(
-                sg->d, SL, nd, (int64_t)so, (int64_t)sp, e->d_mjd, e->d_band, e->d_flux, e->d_fluxerr, e->d_zp,
+                sgu->d, SL, nd, (int64_t)so, (int64_t)sp, e->d_mjd, e->d_band, e->d_flux, e->d_fluxerr, e->d_zp,
                 e->d_t0, e->d_z, e->d_x0, e->d_x1, e->d_c);
             err = cudaGetLastError();
         }
-        if (err == cudaSuccess) err = cudaEventRecord(sg->ev, e->s_up);
-        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
-        sg->busy = true;
-        e->stage_cur ^= 1;
+        if (err == cudaSuccess) err = cudaEventRecord(sgu->ev, e->s_up);
     }
-    if (uploaded) {
+    if (err == cudaSuccess && !adm.empty()) {
         err = cudaEventRecord(e->ev_up, e->s_up);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(e->s_comp, e->ev_up, 0);
-        if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
     }
-    // 4. one launch per (mode, tile) over the admitted requests not yet launched
-    const int chunk = std::max(1, e->ctx->serve_chunk);
     BatchDev b{};
     b.mjd = e->d_mjd; b.band = e->d_band; b.flux = e->d_flux; b.fluxerr = e->d_fluxerr; b.zp = e->d_zp;
     b.t0 = e->d_t0; b.z = e->d_z; b.x0 = e->d_x0; b.x1 = e->d_x1; b.c = e->d_c;
     OutDev o{nullptr, nullptr, e->d_chi2, e->d_grad, e->ctx->err_d};
-    for (int mode = MODE_CHI2; mode <= MODE_GRAD; ++mode) {
-        for (int ti = 0; ti < 4; ++ti) {
-            const int tile = 1 << ti;
-            std::vector<uint64_t> &bucket = e->pending[mode == MODE_GRAD ? 1 : 0][ti];
-            if (bucket.empty()) continue;
-            // while enough launches keep the GPU busy, let requests gather into larger ones
-            if ((int)e->inflight.size() >= e->max_inflight) return true;
-            int slot = -1;
-            for (int q = 0; q < kSlots; ++q)
-                if (!e->slot_busy[q]) { slot = q; break; }
-            if (slot < 0) return true;  // all item buffers in flight: next tick
-            std::vector<uint64_t> members, later;
-            int n_items = 0;
-            for (uint64_t t : bucket) {
-                auto rq = e->reqs.find(t);
-                if (rq == e->reqs.end()) continue;
-                Req &r = *rq->second;
-                if (r.st != St::ACTIVE || r.launched || r.cancel) continue;
-                // a request too large for one item list takes larger chunks
-                const int cr = std::max(chunk, (r.n_par + kMaxItems - 1) / kMaxItems);
-                const int need = (r.n_par + cr - 1) / cr;
-                if (n_items + need > kMaxItems) { later.push_back(t); continue; }
-                for (int j0 = 0; j0 < r.n_par; j0 += cr) {
-                    WorkItem w{};
-                    w.obs0 = (int64_t)r.oo;
-                    w.par0 = (int64_t)r.po + j0;
-                    w.bf0 = 0;
-                    w.nobs = r.n_obs;
-                    w.nj = std::min(cr, r.n_par - j0);
-                    w.jloc0 = j0;
-                    e->items_h[slot][n_items++] = w;
-                }
-                members.push_back(r.ticket);
+    for (size_t gi = 0; gi < grps.size() && err == cudaSuccess; ++gi) {
+        const Grp &G = grps[gi];
+        int n_items = 0;
+        for (const Req *rp : G.members) {
+            const Req &r = *rp;
+            const int cr = std::max(chunk, (r.n_par + kMaxItems - 1) / kMaxItems);
+            for (int j0 = 0; j0 < r.n_par; j0 += cr) {
+                WorkItem w{};
+                w.obs0 = (int64_t)r.oo;
+                w.par0 = (int64_t)r.po + j0;
+                w.bf0 = 0;
+                w.nobs = r.n_obs;
+                w.nj = std::min(cr, r.n_par - j0);
+                w.jloc0 = j0;
+                e->items_h[G.slot][n_items++] = w;
             }
-            bucket.swap(later);
-            if (members.empty()) continue;
-            Launch L;
-            L.slot = slot;
-            L.reqs = members;
-            err = cudaMemcpyAsync(e->items_d[slot], e->items_h[slot], (size_t)n_items * sizeof(WorkItem),
-                                  cudaMemcpyHostToDevice, e->s_comp);
-            if (err == cudaSuccess)
-                err = launch_factorised_items(e->ctx, tile, e->items_d[slot], n_items, e->counters_d + 4 * slot,
-                                              b, o, mode, e->s_comp);
-            if (err == cudaSuccess) err = pool_event(e, &L.ev);
-            if (err == cudaSuccess) err = cudaEventRecord(L.ev, e->s_comp);
-            if (err == cudaSuccess) err = cudaStreamWaitEvent(e->s_down, L.ev, 0);
-            if (err == cudaSuccess) err = download_results(e, members, mode == MODE_GRAD);
-            if (err == cudaSuccess) err = cudaEventRecord(L.ev, e->s_down);
-            if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
-            e->slot_busy[slot] = true;
-            e->n_launches++;
-            for (uint64_t t : members) {
-                Req &r = *e->reqs[t];
-                r.launched = true;
-                r.inflight = 1;
-            }
-            e->inflight.push_back(std::move(L));
+        }
+        err = cudaMemcpyAsync(e->items_d[G.slot], e->items_h[G.slot], (size_t)n_items * sizeof(WorkItem),
+                              cudaMemcpyHostToDevice, e->s_comp);
+        if (err == cudaSuccess)
+            err = launch_factorised_items(e->ctx, G.tile, e->items_d[G.slot], n_items, e->counters_d + 4 * G.slot, b,
+                                          o, G.mode, e->s_comp);
+        if (err == cudaSuccess) err = cudaEventRecord(G.ev, e->s_comp);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->s_down, G.ev, 0);
+        if (err == cudaSuccess) err = download_results(e, G.members, G.mode == MODE_GRAD);
+        if (err == cudaSuccess) err = cudaEventRecord(G.ev, e->s_down);
+    }
+    lk.lock();
+
+    // 5. commit
+    if (sgu && err == cudaSuccess) {
+        sgu->busy = true;
+        e->stage_cur ^= 1;
+    }
+    for (const Adm &ad : adm) {
+        Req &r = *ad.r;
+        r.in.reset();
+        if (r.st == St::ADMITTING) r.st = St::ACTIVE;
+        if (r.cancel && !r.launched && r.st == St::ACTIVE) {
+            // cancelled while being admitted and not in any launch: its upload is
+            // queued before anything that could reuse its ranges
+            release_req(e, r);
+            r.st = St::CANCELLED;
+            e->cv_done.notify_all();
         }
     }
+    for (size_t gi = 0; gi < grps.size(); ++gi) {
+        Launch L;
+        L.slot = grps[gi].slot;
+        L.reqs = std::move(grps[gi].tickets);
+        L.ev = grps[gi].ev;
+        e->inflight.push_back(std::move(L));
+        e->n_launches++;
+    }
+    if (err != cudaSuccess) { fail_all(e, cudaGetErrorString(err)); return false; }
     return true;
 }
 
@@ -531,7 +600,7 @@ void run(ServeEngine *e) {
             e->idle = false;
             continue;
         }
-        tick(e);
+        tick(e, lk);
         // with work queued or in flight the engine comes back on its own after a
         // short wait; submissions meanwhile only queue (they wake an idle engine)
         if (has_work(e)) e->cv_work.wait_for(lk, std::chrono::microseconds(20));
@@ -737,7 +806,7 @@ int serve_stats(ServeEngine *e, salt_serve_stats *out) {
     out->queued = e->queue.size();
     uint64_t act = 0;
     for (auto &kv : e->reqs)
-        if (kv.second->st == St::ACTIVE) act++;
+        if (kv.second->st == St::ACTIVE || kv.second->st == St::ADMITTING) act++;
     out->active = act;
     out->mem_in_use = e->obs_a.used() * kObsBytes + e->par_a.used() * kParBytes;
     out->mem_limit = e->obs_a.size() * kObsBytes + e->par_a.size() * kParBytes;
