@@ -388,7 +388,7 @@ def sampled_oracle(wl, s, db, stream, n_picks=None, budget_s=None, results=None)
     gradient: `results` = (chi2, grad) device tensors of a timed step, else a
     new salt_chi2_grad call; bandfluxes: a full-batch salt_bandflux call).
     The number of pairs is n_picks, or, with budget_s, what fills about that
-    many seconds of oracle time at the rate measured on a first 64 pairs. The
+    many seconds of oracle time at the rate measured on a first 512 pairs. The
     first and last sample of the batch are always among them."""
     import torch
     import oracle
@@ -407,12 +407,13 @@ def sampled_oracle(wl, s, db, stream, n_picks=None, budget_s=None, results=None)
         return p, sn, sub
 
     if budget_s is not None:
-        _, _, cal = pairs(64)
+        # calibration on enough pairs to keep every host thread busy
+        _, _, cal = pairs(512)
         t0 = time.perf_counter()
         o.chi2(cal, grad=True)
         rate = cal.n_bandflux() / max(time.perf_counter() - t0, 1e-6)
         per_pair = bt.n_bandflux() / max(bt.n_par, 1)
-        n_picks = int(np.clip(budget_s * rate / per_pair, 64, 16384))
+        n_picks = int(np.clip(budget_s * rate / per_pair, 64, 32768))
     picks, sn_of, sub = pairs(n_picks)
     with torch.cuda.stream(stream):
         x2, g = results if results is not None else s.chi2_grad(db)

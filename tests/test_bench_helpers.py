@@ -66,3 +66,43 @@ def test_error_measures():
     worse = bench.error_vs_oracle(bt, (x2, ref[1], bf), ref)
     np.testing.assert_allclose(worse["chi2_max_rel"], 3e-4, rtol=1e-6)
     assert worse["bandflux_max_rel"] >= 2e-3 * 0.99
+
+
+def test_sampled_oracle_pairs_and_errors(monkeypatch):
+    """The CPU-baseline leg for batches too large for the oracle: the seeded
+    pairs include the batch's first and last sample, each pair's bandfluxes
+    are taken from the right positions of a full-batch bandflux array, and the
+    error measures see exactly the planted differences. The library is
+    replaced by the oracle's own full-batch results (no GPU)."""
+    import contextlib
+    import torch
+    import oracle
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a: None)
+    wl = W.config3(n_sn=5, n_samples=7)
+    W.template_flux(wl.batch, np.random.default_rng(1))
+    o = oracle.Oracle(wl.model, wl.bands)
+    x2, g = o.chi2(wl.batch, grad=True)
+    bf = o.bandflux(wl.batch)
+    x2_bad = x2.copy()
+    x2_bad[-1] *= 1 + 5e-4   # the last sample of the batch: always among the pairs
+
+    class FakeLib:
+        def chi2_grad(self, db):
+            return torch.tensor(x2_bad), torch.tensor(g, dtype=torch.float32)
+
+        def bandflux(self, db):
+            return torch.tensor(bf, dtype=torch.float32)
+
+    r = bench.sampled_oracle(wl, FakeLib(), None, None, n_picks=12)
+    e = r["error_vs_oracle"]
+    assert e["samples_compared"] >= 12 and r["kind"] == "oracle"
+    np.testing.assert_allclose(e["chi2_max_rel"], 5e-4, rtol=1e-9)
+    assert e["bandflux_max_rel"] < 1e-7 and e["grad_max_scaled"] < 1e-6
+    # the same through the results of a timed step, with a sample budget
+    r2 = bench.sampled_oracle(wl, FakeLib(), None, None, budget_s=0.05,
+                              results=(torch.tensor(x2), torch.tensor(g, dtype=torch.float32)))
+    assert r2["error_vs_oracle"]["chi2_max_rel"] == 0.0
+    assert r2["error_vs_oracle"]["samples_compared"] >= 64 or \
+        r2["error_vs_oracle"]["samples_compared"] == wl.batch.n_par
