@@ -30,8 +30,9 @@ typedef struct {
 /* Replay n requests against ctx's serving engine: one thread submits
  * request i at arrival_s[i] seconds after the start (all at once when
  * arrival_s is NULL; arrivals nondecreasing), another sweeps the oldest
- * outstanding requests (up to 32 at a time) with non-blocking polls and
- * takes each result as soon as it is ready. Results go to chi2_out[i] (HOST float64 [n_par]) and
+ * outstanding requests (up to 32 at a time) with non-blocking polls, backing
+ * off 20 us after a sweep that finds nothing, and takes each result when it is
+ * ready. Results go to chi2_out[i] (HOST float64 [n_par]) and
  * grad_out[i] (HOST float32 [n_par][5], requests with want_grad) when those
  * arrays and entries are non-NULL, else to a scratch buffer. lat_ms
  * (nullable, [n]) receives each request's client latency. Returns the first

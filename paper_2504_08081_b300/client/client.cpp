@@ -94,7 +94,8 @@ extern "C" int salt_client_replay(salt_ctx *ctx, const salt_request *reqs, int32
 
     // The poller sweeps, without waiting, the oldest outstanding requests (a
     // window of kWin), so a request's completion time is taken when its own
-    // results are ready, not after the slower requests submitted before it.
+    // results are ready (within the back-off below), not after the slower
+    // requests submitted before it.
     constexpr int kWin = 32;
     std::vector<double> chi2_tmp((size_t)max_par);
     std::vector<float> grad_tmp(5 * (size_t)max_par);
@@ -124,7 +125,9 @@ extern "C" int salt_client_replay(salt_ctx *ctx, const salt_request *reqs, int32
             }
         }
         while (head < n && fin[(size_t)head]) ++head;
-        if (!progress) std::this_thread::yield();
+        // nothing ready: back off briefly, so the polls do not keep the engine
+        // lock from the submitting thread and the scheduler
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     submitter.join();
     const Clock::time_point t_end = Clock::now();
