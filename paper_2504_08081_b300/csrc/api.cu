@@ -135,6 +135,9 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     mp.phase0 = (float)p0;
     mp.inv_dphase = (float)(md->phase_nodes ? (md->n_phase - 1) / (p1 - p0) : 1.0 / md->dphase);
     mp.phase_max = (float)p1;
+    mp.dphase = (float)(md->phase_nodes ? 1.0 : md->dphase);
+    mp.phase0_d = p0;
+    mp.inv_dphase_d = md->phase_nodes ? (md->n_phase - 1) / (p1 - p0) : 1.0 / md->dphase;
     mp.wave0 = (float)w0;
     mp.inv_dwave = (float)(md->wave_nodes ? (md->n_wave - 1) / (w1 - w0) : 1.0 / md->dwave);
     mp.wave_max = (float)w1;
@@ -199,21 +202,28 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
             return fail(e, "upload bands");
     }
     if (md->phase_nodes || md->wave_nodes) {
-        // [phase nodes | phase inverse widths | wave nodes | wave inverse widths], each n long
+        // [phase nodes | phase inverse widths | wave nodes | wave inverse widths | phase node
+        // remainders], each n long
         const int np = md->n_phase, nw = md->n_wave;
-        std::vector<float> nodes(2 * (size_t)np + 2 * (size_t)nw, 0.f);
+        std::vector<float> nodes(3 * (size_t)np + 2 * (size_t)nw, 0.f);
         auto fill = [&](const double *x, int n, float *node, float *inv) {
             for (int i = 0; i < n; ++i) node[i] = (float)x[i];
             for (int i = 0; i + 1 < n; ++i) inv[i] = (float)(1.0 / (x[i + 1] - x[i]));
         };
         if (md->phase_nodes) fill(md->phase_nodes, np, nodes.data(), nodes.data() + np);
         if (md->wave_nodes) fill(md->wave_nodes, nw, nodes.data() + 2 * np, nodes.data() + 2 * np + nw);
+        if (md->phase_nodes) {
+            float *rem = nodes.data() + 2 * np + 2 * nw;
+            for (int i = 0; i < np; ++i) rem[i] = (float)(md->phase_nodes[i] - (double)nodes[i]);
+        }
         if ((e = cudaMalloc(&ctx->nodes_d, nodes.size() * sizeof(float))) != cudaSuccess)
             return fail(e, "cudaMalloc nodes");
         if ((e = cudaMemcpy(ctx->nodes_d, nodes.data(), nodes.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
             return fail(e, "upload nodes");
-        if (md->phase_nodes) { mp.pnode = ctx->nodes_d; mp.pinv = ctx->nodes_d + np; }
+        if (md->phase_nodes) {
+            mp.pnode = ctx->nodes_d; mp.pinv = ctx->nodes_d + np; mp.pnode_lo = ctx->nodes_d + 2 * np + 2 * nw;
+        }
         if (md->wave_nodes) { mp.wnode = ctx->nodes_d + 2 * np; mp.winv = ctx->nodes_d + 2 * np + nw; }
     }
     if ((e = cudaMalloc(&ctx->err_d, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");

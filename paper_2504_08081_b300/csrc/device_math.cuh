@@ -109,20 +109,98 @@ __device__ __forceinline__ void axis_taps(float x, float x0, float inv_dx, float
     axis_taps_from<DERIV>(i, t, n, inv_dx, tp);
 }
 
-// The model's two axes.
-__device__ __forceinline__ bool phase_find(const ModelParams &m, float p, int &i, float &t, float &iw) {
-    return axis_find(p, m.phase0, m.inv_dphase, m.phase_max, m.n_phase, m.pnode, m.pinv, i, t, iw);
+// ---- The phase coordinate as a float pair.
+// The rest-frame phase (mjd - t0) / (1 + z) is a difference of epochs ~5e4 d
+// apart by tens of days. Formed in FP32, the phase (or its grid coordinate
+// near the end of a 70-node axis) carries ~4e-6 d of rounding, which the steep
+// ends of a surface turn into ~1e-5 of bandflux. So the observation time is
+// held as a float pair (hi + lo = mjd to ~1e-10 d), each sample has an origin
+// O and a scale S (FP64 per sample, stored as float pairs) with
+// u = (mjd - O) S, and u is formed as a float pair by error-free
+// transformations (Knuth's two-sum, the FMA product error): FP32 arithmetic
+// throughout, no FP64 per (observation, sample) pair. On a uniform axis u is
+// the grid coordinate (O = t0 + phase0 (1 + z), S = 1 / ((1 + z) dphase));
+// on a node axis it is the phase itself (O = t0, S = 1 / (1 + z)).
+
+// x as hi + lo, hi = x rounded to FP32.
+__device__ __forceinline__ float2 split_f2(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
 }
+
+// Per-sample phase map (O hi, O lo, S hi, S lo); a = 1 / (1 + z) rounded once.
+__device__ __forceinline__ float4 phase_map(const ModelParams &m, float z, double t0, float &a) {
+    const double zp1 = 1.0 + (double)z;
+    const double ad = 1.0 / zp1;
+    a = __double2float_rn(ad);
+    double o = t0, s = ad;
+    if (!m.pnode) { o = fma(m.phase0_d, zp1, t0); s = ad * m.inv_dphase_d; }
+    const float2 O = split_f2(o), S = split_f2(s);
+    return make_float4(O.x, O.y, S.x, S.y);
+}
+
+// u = (tm - O) S as a normalised float pair (x + y, |y| <= ulp(x) / 2 when
+// |u| is not tiny). The _rn intrinsics keep the compiler from fusing the
+// products into the sums the error terms are taken from.
+__device__ __forceinline__ float2 phase_u(float2 tm, float4 pm) {
+    const float dh = __fadd_rn(tm.x, -pm.x);                // two-sum of tm.x and -O.x
+    const float bv = __fadd_rn(dh, -tm.x);
+    const float de = __fadd_rn(__fadd_rn(tm.x, -__fadd_rn(dh, -bv)), -__fadd_rn(pm.x, bv));
+    const float dl = __fadd_rn(de, __fadd_rn(tm.y, -pm.y)); // tm - O = dh + dl
+    const float uh = __fmul_rn(dh, pm.z);
+    float ue = fmaf(dh, pm.z, -uh);                         // exact error of dh S.hi
+    ue = fmaf(dh, pm.w, ue);
+    ue = fmaf(dl, pm.z, ue);
+    const float s = __fadd_rn(uh, ue);                      // fast two-sum
+    return make_float2(s, __fadd_rn(ue, -__fadd_rn(s, -uh)));
+}
+
+// Interval i, fraction t and inverse width iw (as axis_find) of the phase of
+// observation time tm under the sample's phase map pm, the interval chosen
+// and t formed from the float pair; p is the phase in FP32 (for the gradient
+// terms). False outside the phase axis.
+__device__ __forceinline__ bool phase_find(const ModelParams &m, float2 tm, float4 pm, int &i, float &t, float &iw,
+                                           float &p) {
+    const float2 u = phase_u(tm, pm);
+    if (!m.pnode) {
+        const float top = (float)(m.n_phase - 1);
+        if (!((u.x > 0.f || (u.x == 0.f && u.y >= 0.f)) && (u.x < top || (u.x == top && u.y <= 0.f))))
+            return false;
+        i = min(__float2int_rd(u.x), m.n_phase - 2);
+        t = __fadd_rn(u.x, -(float)i) + u.y;  // u.x - i is exact
+        iw = m.inv_dphase;
+        p = fmaf(u.x, m.dphase, m.phase0);
+        return true;
+    }
+    const int n = m.n_phase;
+    const float n0 = __ldg(m.pnode), n1 = __ldg(m.pnode + n - 1);
+    const float l0 = __ldg(m.pnode_lo), l1 = __ldg(m.pnode_lo + n - 1);
+    if (!((u.x > n0 || (u.x == n0 && u.y >= l0)) && (u.x < n1 || (u.x == n1 && u.y <= l1)))) return false;
+    int lo = 0, hi = n - 1;  // node[lo] <= u.x <= node[hi] (float parts)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m.pnode + mid) <= u.x) lo = mid; else hi = mid;
+    }
+    i = lo;
+    iw = __ldg(m.pinv + lo);
+    // (u - node) from the pairs: the hi difference is exact or rounded relative
+    // to itself (at most one interval)
+    t = fminf((__fadd_rn(u.x, -__ldg(m.pnode + lo)) + (u.y - __ldg(m.pnode_lo + lo))) * iw, 1.0f);
+    p = u.x;
+    return true;
+}
+
 __device__ __forceinline__ bool wave_find(const ModelParams &m, float lam, int &i, float &t, float &iw) {
     return axis_find(lam, m.wave0, m.inv_dwave, m.wave_max, m.n_wave, m.wnode, m.winv, i, t, iw);
 }
 
 // Taps on a model axis (all weights zero outside it).
 template <bool DERIV>
-__device__ __forceinline__ void phase_taps(const ModelParams &m, float p, Taps4 &tp) {
+__device__ __forceinline__ void phase_taps(const ModelParams &m, float2 tm, float4 pm, Taps4 &tp, float &p) {
     int i;
     float t, iw;
-    if (!phase_find(m, p, i, t, iw)) {
+    p = 0.f;
+    if (!phase_find(m, tm, pm, i, t, iw, p)) {
         tp.first = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) { tp.w[q] = 0.f; if (DERIV) tp.dw[q] = 0.f; }

@@ -24,7 +24,7 @@ constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memo
 using fk::al16;
 
 struct Lay {
-    size_t ord, zpf, band, mjd, flux, sig, bst, pj, t0, slots, misc, lam, wk, warp0, warp_bytes, total;
+    size_t ord, zpf, band, mjd, flux, sig, bst, pj, pm, slots, misc, lam, wk, warp0, warp_bytes, total;
     __host__ __device__ Lay(int ts, bool grad, int nb) {
         size_t o = 0;
         ord = o;   o = al16(o + 4 * OBS_MAX);
@@ -35,7 +35,7 @@ struct Lay {
         sig = o;   o = al16(o + 4 * OBS_MAX);
         bst = o;   o = al16(o + 4 * (2 * SALT_MAX_BANDS + 2));
         pj = o;    o = al16(o + 4 * 8 * NJ_MAX);
-        t0 = o;    o = al16(o + 8 * NJ_MAX);
+        pm = o;    o = al16(o + 16 * NJ_MAX);
         slots = o; o = al16(o + 8 * (size_t)NSLOT * NJ_MAX * (nb > 0 ? nb : 1));
         misc = o;  o = al16(o + 4 * (16 + SALT_MAX_BANDS));
         lam = o;   o = al16(o + 4 * KTOT);
@@ -62,12 +62,12 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
     int *sOrd = (int *)(smem + L.ord);
     float *sZpf = (float *)(smem + L.zpf);
     int *sBand = (int *)(smem + L.band);
-    double *sMjd = (double *)(smem + L.mjd);
+    float2 *sMjd = (float2 *)(smem + L.mjd);  // observation times as float pairs
     float *sFlux = (float *)(smem + L.flux);
     float *sSig = (float *)(smem + L.sig);
     int *sBst = (int *)(smem + L.bst);
     float *sPj = (float *)(smem + L.pj);  // [5][NJ_MAX]
-    double *sT0 = (double *)(smem + L.t0);
+    float4 *sPm = (float4 *)(smem + L.pm);    // [NJ_MAX] phase maps
     double *sSlot = (double *)(smem + L.slots);  // [NJ_MAX][NB][NSLOT]
     int *sMisc = (int *)(smem + L.misc);
     int *sPresent = sMisc + 16;  // present band ids, in band order
@@ -119,12 +119,13 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                 if (!ok) atomicOr(o.err, ERRBIT_PARAM);
             }
             if (!ok) { z = 0.f; x0 = 0.f; x1 = 0.f; c = 0.f; t0 = 0.0; }
-            sPj[PJ_A * NJ_MAX + j] = 1.0f / (1.0f + z);
+            float a;
+            sPm[j] = phase_map(m, z, t0, a);
+            sPj[PJ_A * NJ_MAX + j] = a;
             sPj[PJ_X0 * NJ_MAX + j] = x0;
             sPj[PJ_X1 * NJ_MAX + j] = x1;
             sPj[PJ_C * NJ_MAX + j] = c;
             sPj[PJ_OK * NJ_MAX + j] = (j < nj && ok) ? 1.f : 0.f;
-            sT0[j] = t0;
         }
         if (tid == 0) sMisc[2] = 0;
         for (int q = tid; q < NSLOT * NJ_MAX * NB; q += THREADS) sSlot[q] = 0.0;
@@ -145,7 +146,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                 }
                 sZpf[i] = zp_scale(b.zp[obase + i]);
                 sBand[i] = (okb && e > 0.f) ? bd : -1;
-                sMjd[i] = b.mjd[obase + i];
+                sMjd[i] = split_f2(b.mjd[obase + i]);
                 sFlux[i] = b.flux[obase + i];
                 sSig[i] = e;
             }
@@ -242,13 +243,12 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     const int il = base + lane;
                     if (il < nb_obs) {
                         const int i = ordb[il];
-                        const double mj = sMjd[i];
+                        const float2 mj = sMjd[i];
 #pragma unroll
                         for (int s = 0; s < TS; ++s) {
                             if (s >= ns || sPj[PJ_OK * NJ_MAX + j0 + s] == 0.f) continue;
-                            const float p = (float)(mj - sT0[j0 + s]) * sPj[PJ_A * NJ_MAX + j0 + s];
-                            int iv; float t, iwp;
-                            if (phase_find(m, p, iv, t, iwp)) {
+                            int iv; float t, iwp, p;
+                            if (phase_find(m, mj, sPm[j0 + s], iv, t, iwp, p)) {
                                 const int first = fk::first_tap(iv, NP);
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) msk[(first + q) >> 5] |= 1u << ((first + q) & 31);
@@ -350,7 +350,7 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                     const int il = base + lane;
                     const bool act = il < nb_obs;
                     const int i = act ? ordb[il] : 0;
-                    const double mj = act ? sMjd[i] : 0.0;
+                    const float2 mj = act ? sMjd[i] : make_float2(0.f, 0.f);
                     const float zpf = act ? sZpf[i] : 0.f;
                     const float fl = (act && MODE != MODE_BANDFLUX) ? sFlux[i] : 0.f;
                     const float sig = (act && MODE != MODE_BANDFLUX) ? sSig[i] : 1.f;
@@ -364,9 +364,8 @@ k_bandwarp(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ ite
                         if (act && s < ns) {
                             const float a = sPj[PJ_A * NJ_MAX + j], x0 = sPj[PJ_X0 * NJ_MAX + j];
                             const float x1 = sPj[PJ_X1 * NJ_MAX + j];
-                            const float p = (float)(mj - sT0[j]) * a;
-                            int iv; float t, iwp;
-                            if (okj && phase_find(m, p, iv, t, iwp)) {
+                            int iv; float t, iwp, p = 0.f;
+                            if (okj && phase_find(m, mj, sPm[j], iv, t, iwp, p)) {
                                 axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                                 for (int mm = 0; mm < 4; ++mm) {

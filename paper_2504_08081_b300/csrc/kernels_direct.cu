@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) k_direct(ModelParams m, BatchDev b, OutDe
     const float z = b.z[j], x0 = b.x0[j], x1 = b.x1[j], c = b.c[j];
     const double t0 = b.t0[j];
     bool bad = !params_ok(z, t0, x0, x1, c);
-    const float a = 1.0f / (1.0f + z);
+    float a;
+    const float4 pm = phase_map(m, bad ? 0.f : z, bad ? 0.0 : t0, a);
     double chi2 = 0.0;
     float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int64_t i = i0; i < i1; ++i) {
@@ -47,9 +48,9 @@ __global__ void __launch_bounds__(256) k_direct(ModelParams m, BatchDev b, OutDe
                 o.bandflux[o.bf_off[s] + jl * (i1 - i0) + (i - i0)] = __int_as_float(0x7fc00000);
             continue;
         }
-        const float p = (float)(b.mjd[i] - t0) * a;
         Taps4 tp;
-        phase_taps<GRAD>(m, p, tp);
+        float p;
+        phase_taps<GRAD>(m, split_f2(b.mjd[i]), pm, tp, p);
         float accB = 0.f, acc1 = 0.f, accC = 0.f, accP = 0.f, accL = 0.f;
         const int off = m.bands.off[bnd], K = m.bands.n[bnd];
         for (int k = lane; k < K; k += 32) {

@@ -38,7 +38,7 @@ constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memo
 
 
 struct Lay {
-    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, t0, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, total;
+    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, pm, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, total;
     __host__ __device__ Lay(int tj, bool grad, int n_phase) {
         const int wps = tj >= WARPS ? 1 : WARPS / tj;
         const int nslot = tj > WARPS ? tj : WARPS;  // (warp, sample) slots
@@ -54,7 +54,7 @@ struct Lay {
         lam = o;     o = al16(o + (stage ? 4 * KTOT : 0));
         wk = o;      o = al16(o + (stage ? 4 * KTOT : 0));
         pj = o;      o = al16(o + 4 * 8 * tj);
-        t0 = o;      o = al16(o + 8 * tj);
+        pm = o;      o = al16(o + 16 * tj);
         rowmask = o; o = al16(o + 4 * (NPH_MAX / 32));
         rows = o;    o = al16(o + 4 * NPH_MAX);
         misc = o;    o = al16(o + 4 * 16);
@@ -155,7 +155,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *sLam = (float *)(smem + L.lam);
     float *sWk = (float *)(smem + L.wk);
     float *sPj = (float *)(smem + L.pj);    // [PJ_NUM][TJ]
-    double *sT0 = (double *)(smem + L.t0);  // [TJ]
+    float4 *sPm = (float4 *)(smem + L.pm);  // [TJ] phase maps
     unsigned *sRowMask = (unsigned *)(smem + L.rowmask);
     int *sRows = (int *)(smem + L.rows);
     int *sMisc = (int *)(smem + L.misc);
@@ -164,7 +164,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *sQ = (float *)(smem + L.Q);     // [THREADS][TJ] reverse-GEMM partials, then Q[col][j]
     float *sD = (float *)(smem + L.D);     // [n_phase][TJ][2]
     float *sYw = (float *)(smem + L.Yw);   // [slots][n_phase] adjoint rows per (warp, sample)
-    double *sMjd = (double *)(smem + L.mjd);
+    float2 *sMjd = (float2 *)(smem + L.mjd);  // observation times as float pairs
     int *sBand = (int *)(smem + L.band);
     float *sFlux = (float *)(smem + L.flux);
     float *sSig = (float *)(smem + L.sig);  // 1 / fluxerr
@@ -222,12 +222,13 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     if (!ok) atomicOr(o.err, ERRBIT_PARAM);
                 }
                 if (!ok) { z = 0.f; x0 = 0.f; x1 = 0.f; c = 0.f; t0 = 0.0; }
-                sPj[PJ_A * TJ + j] = 1.0f / (1.0f + z);
+                float a;
+                sPm[j] = phase_map(m, z, t0, a);
+                sPj[PJ_A * TJ + j] = a;
                 sPj[PJ_X0 * TJ + j] = x0;
                 sPj[PJ_X1 * TJ + j] = x1;
                 sPj[PJ_C * TJ + j] = c;
                 sPj[PJ_OK * TJ + j] = (j < nj && ok) ? 1.f : 0.f;
-                sT0[j] = t0;
             }
             // per-lane accumulators with a fixed assignment (deterministic sums):
             // warp w owns sample w / WPS in the epilogue and the reverse dot
@@ -259,7 +260,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     }
                     sZpf[i] = zp_scale(b.zp[obase + i]);
                     sBand[i] = (okb && e > 0.f) ? bd : -1;
-                    sMjd[i] = b.mjd[obase + i];
+                    sMjd[i] = split_f2(b.mjd[obase + i]);
                     sFlux[i] = b.flux[obase + i];
                     sSig[i] = 1.0f / e;  // 1/sigma (never used when e <= 0: band id -1)
                 }
@@ -354,9 +355,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             const int il = q / nj, j = q - il * nj;
                             if (sPj[PJ_OK * TJ + j] != 0.f) {
                                 const int i = ordb[il];
-                                const float p = (float)(sMjd[i] - sT0[j]) * sPj[PJ_A * TJ + j];
-                                int iv; float t, iwp;
-                                if (phase_find(m, p, iv, t, iwp))
+                                int iv; float t, iwp, p;
+                                if (phase_find(m, sMjd[i], sPm[j], iv, t, iwp, p))
                                     first = first_tap(iv, NP);
                             }
                         }
@@ -467,7 +467,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             const bool okj = sPj[PJ_OK * TJ + j] != 0.f;
                             const float a = sPj[PJ_A * TJ + j], x0 = sPj[PJ_X0 * TJ + j];
                             const float x1 = sPj[PJ_X1 * TJ + j];
-                            const double t0 = sT0[j];
+                            const float4 pm = sPm[j];
                             float *yw = sYw + (warp * SPW + jj) * NP;
                             for (int base = sub * 32; base < nb_obs; base += 32 * WPS) {
                                 const int il = base + lane;
@@ -477,9 +477,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 float Bs = 0.f, Bp = 0.f, B1 = 0.f, coef = 0.f;
                                 if (act) {
                                     const int i = ordb[il];
-                                    const float p = (float)(sMjd[i] - t0) * a;
-                                    int iv; float t, iwp;
-                                    if (okj && phase_find(m, p, iv, t, iwp)) {
+                                    int iv; float t, iwp, p = 0.f;
+                                    if (okj && phase_find(m, sMjd[i], pm, iv, t, iwp, p)) {
                                         axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                                         for (int mm = 0; mm < 4; ++mm) {

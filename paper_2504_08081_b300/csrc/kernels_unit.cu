@@ -128,7 +128,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     const int NB = m.bands.n_bands, NW = m.n_wave, NP = m.n_phase;
     unsigned char *wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
     int *oIdx = (int *)wb;                                     wb += al16(4 * OBS_W);
-    double *oMjd = (double *)wb;                               wb += al16(8 * OBS_W);
+    float2 *oMjd = (float2 *)wb;                               wb += al16(8 * OBS_W);
     float *oFlux = (float *)wb;                                wb += al16(4 * OBS_W);
     float *oSig = (float *)wb;                                 wb += al16(4 * OBS_W);
     float *oZpf = (float *)wb;                                 wb += al16(4 * OBS_W);
@@ -154,17 +154,17 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
 
         // per-sample parameters (uniform across the warp)
         float pa[TS], px0[TS], px1[TS], pc[TS];
-        double pt0[TS];
+        float4 ppm[TS];  // phase maps
         bool pok[TS];
 #pragma unroll
         for (int s = 0; s < TS; ++s) {
-            pa[s] = 1.f; px0[s] = 0.f; px1[s] = 0.f; pc[s] = 0.f; pt0[s] = 0.0; pok[s] = false;
+            pa[s] = 1.f; px0[s] = 0.f; px1[s] = 0.f; pc[s] = 0.f; ppm[s] = make_float4(0.f, 0.f, 0.f, 0.f); pok[s] = false;
             if (s < ns) {
                 const int64_t g = wi.par0 + s;
                 const float z = b.z[g], x0 = b.x0[g], x1 = b.x1[g], c = b.c[g];
                 const double t0 = b.t0[g];
                 pok[s] = isfinite(z) && z > -1.f && isfinite(x0) && isfinite(x1) && isfinite(c) && isfinite(t0);
-                if (pok[s]) { pa[s] = 1.0f / (1.0f + z); px0[s] = x0; px1[s] = x1; pc[s] = c; pt0[s] = t0; }
+                if (pok[s]) { ppm[s] = phase_map(m, z, t0, pa[s]); px0[s] = x0; px1[s] = x1; pc[s] = c; }
                 else if (lane == 0 && bd == 0) atomicOr(o.err, ERRBIT_PARAM);
             }
         }
@@ -280,7 +280,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             // the rest of the pass's observations, loaded together (independent loads)
             for (int q = lane; q < nb_obs; q += 32) {
                 const int64_t gi = ob0 + oIdx[q];
-                oMjd[q] = b.mjd[gi];
+                oMjd[q] = split_f2(b.mjd[gi]);
                 oFlux[q] = b.flux[gi];
                 oZpf[q] = zp_scale(b.zp[gi]);
             }
@@ -294,9 +294,8 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
 #pragma unroll
                     for (int s = 0; s < TS; ++s) {
                         if (!pok[s]) continue;
-                        const float p = (float)(oMjd[il] - pt0[s]) * pa[s];
-                        int iv; float t, iwp;
-                        if (phase_find(m, p, iv, t, iwp)) {
+                        int iv; float t, iwp, p;
+                        if (phase_find(m, oMjd[il], ppm[s], iv, t, iwp, p)) {
                             const int first = fk::first_tap(iv, NP);
                             const int w0 = first >> 5, sh = first & 31;
                             const unsigned lo = 0xfu << sh;                       // rows in word w0
@@ -404,7 +403,7 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
             for (int base = 0; base < nb_obs; base += 32) {
                 const int il = base + lane;
                 const bool act = il < nb_obs;
-                const double mj = act ? oMjd[il] : 0.0;
+                const float2 mj = act ? oMjd[il] : make_float2(0.f, 0.f);
                 const float zpf = act ? oZpf[il] : 0.f;
                 const float fl = act ? oFlux[il] : 0.f;
                 const float sig = act ? oSig[il] : 1.f;
@@ -414,9 +413,8 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     float Bs = 0.f, Bp = 0.f, B1 = 0.f, Bc = 0.f, Bz = 0.f;
                     if (act && s < ns) {
                         const float a = pa[s];
-                        const float p = (float)(mj - pt0[s]) * a;
-                        int iv; float t, iwp;
-                        if (pok[s] && phase_find(m, p, iv, t, iwp)) {
+                        int iv; float t, iwp, p = 0.f;
+                        if (pok[s] && phase_find(m, mj, ppm[s], iv, t, iwp, p)) {
                             axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
 #pragma unroll
                             for (int mm = 0; mm < 4; ++mm) {

@@ -39,6 +39,8 @@ struct ModelParams {
     int n_phase, n_wave;
     int nw_pitch;  // row pitch of g01 in float2 (n_wave rounded up to even: 16-byte aligned rows)
     float phase0, inv_dphase, phase_max;
+    float dphase;                   // uniform phase step (for the phase itself, gradient terms)
+    double phase0_d, inv_dphase_d;  // the same in FP64 (per-sample phase maps)
     float wave0, inv_dwave, wave_max, dwave;
     // colour law: P(x) = sum_{m=1..5} p[m-1] x^m, x = (lambda - lamB) * inv_span
     float cl_p[5];
@@ -50,6 +52,7 @@ struct ModelParams {
     // non-uniform axes (NULL = uniform): node positions and 1/(node[i+1] - node[i])
     const float *__restrict__ pnode;
     const float *__restrict__ pinv;
+    const float *__restrict__ pnode_lo;  // node - (float)node: phase nodes as float pairs
     const float *__restrict__ wnode;
     const float *__restrict__ winv;
     BandTable bands;
