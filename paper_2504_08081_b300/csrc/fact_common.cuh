@@ -44,6 +44,81 @@ __device__ __forceinline__ void ebuild_point(const ModelParams &m, const float *
     for (int q = 0; q < 4; ++q) v[q] = A * tl.w[q];
 }
 
+// ---- Two band samples at once through the packed FP32 instructions
+// (fma/mul/add .f32x2): each half is the IEEE operation of the scalar code,
+// in the same order, so the values are those of one band sample at a time.
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// keys_weights on both halves.
+__device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4]) {
+    const float2 t2 = __fmul2_rn(t, t);
+    w[0] = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(f2(-0.5f), t, f2(1.0f)), f2(-0.5f)));
+    w[1] = __ffma2_rn(t2, __ffma2_rn(f2(1.5f), t, f2(-2.5f)), f2(1.0f));
+    w[2] = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(f2(-1.5f), t, f2(2.0f)), f2(0.5f)));
+    w[3] = __fmul2_rn(t2, __ffma2_rn(f2(0.5f), t, f2(-0.5f)));
+}
+
+// colour_law on both halves (value; with DERIV also dCL/dlambda).
+template <bool DERIV>
+__device__ __forceinline__ float2 colour_law2(const ModelParams &m, float2 lam, float2 &dcl) {
+    const float2 x = __fmul2_rn(__fadd2_rn(lam, f2(-m.cl_lamB)), f2(m.cl_inv_span));
+    const float *p = m.cl_p;
+    const float2 Pin = __fmul2_rn(
+        x, __ffma2_rn(x, __ffma2_rn(x, __ffma2_rn(x, __ffma2_rn(x, f2(p[4]), f2(p[3])), f2(p[2])), f2(p[1])),
+                      f2(p[0])));
+    const float2 Plo = __ffma2_rn(f2(m.cl_dPlo), __fadd2_rn(x, f2(-m.cl_xlo)), f2(m.cl_Plo));
+    const float2 Phi = __ffma2_rn(f2(m.cl_dPhi), __fadd2_rn(x, f2(-m.cl_xhi)), f2(m.cl_Phi));
+    const bool la = lam.x < m.cl_lo, lb = lam.y < m.cl_lo, ha = lam.x > m.cl_hi, hb = lam.y > m.cl_hi;
+    if (DERIV) {
+        const float2 dPin = __ffma2_rn(
+            x, __ffma2_rn(x, __ffma2_rn(x, __ffma2_rn(x, f2(5.f * p[4]), f2(4.f * p[3])), f2(3.f * p[2])),
+                          f2(2.f * p[1])),
+            f2(p[0]));
+        const float2 dP = make_float2(la ? m.cl_dPlo : (ha ? m.cl_dPhi : dPin.x),
+                                      lb ? m.cl_dPlo : (hb ? m.cl_dPhi : dPin.y));
+        dcl = __fmul2_rn(dP, f2(-m.cl_inv_span));
+    }
+    return make_float2(-(la ? Plo.x : (ha ? Phi.x : Pin.x)), -(lb ? Plo.y : (hb ? Phi.y : Pin.y)));
+}
+
+// Interval and fraction of both halves on the uniform wavelength axis
+// (in-grid wavelengths: the arithmetic of axis_locate).
+__device__ __forceinline__ float2 wave_locate2(const ModelParams &m, float2 lr, int &ia, int &ib) {
+    const float2 u = __fmul2_rn(__fadd2_rn(lr, f2(-m.wave0)), f2(m.inv_dwave));
+    ia = min(max(__float2int_rd(u.x), 0), m.n_wave - 2);
+    ib = min(max(__float2int_rd(u.y), 0), m.n_wave - 2);
+    return __fadd2_rn(u, make_float2(-(float)ia, -(float)ib));
+}
+
+// ebuild_point for two in-grid band samples (uniform wavelength axis), kc =
+// kColour * c: first tap columns fa, fb and the weighted taps, halves (a, b).
+__device__ __forceinline__ void ebuild_point2(const ModelParams &m, float2 lamk, float2 wkk, float a, float kc,
+                                              int &fa, int &fb, float2 (&v)[4]) {
+    const int NW = m.n_wave;
+    const float2 lr = __fmul2_rn(lamk, f2(a));
+    int ia, ib;
+    const float2 t = wave_locate2(m, lr, ia, ib);
+    float2 kw[4];
+    keys_weights2(t, kw);
+    const float2 l0 = __ffma2_rn(t, f2(-1.0f), f2(1.0f));
+    const bool ea = ia == 0 || ia == NW - 2, eb = ib == 0 || ib == NW - 2, loa = ia == 0, lob = ib == 0;
+    fa = ea ? (loa ? 0 : NW - 4) : ia - 1;
+    fb = eb ? (lob ? 0 : NW - 4) : ib - 1;
+    const float2 w0 = make_float2(ea ? (loa ? l0.x : 0.f) : kw[0].x, eb ? (lob ? l0.y : 0.f) : kw[0].y);
+    const float2 w1 = make_float2(ea ? (loa ? t.x : 0.f) : kw[1].x, eb ? (lob ? t.y : 0.f) : kw[1].y);
+    const float2 w2 = make_float2(ea ? (loa ? 0.f : l0.x) : kw[2].x, eb ? (lob ? 0.f : l0.y) : kw[2].y);
+    const float2 w3 = make_float2(ea ? (loa ? 0.f : t.x) : kw[3].x, eb ? (lob ? 0.f : t.y) : kw[3].y);
+    float2 dcl_;
+    const float2 cl = colour_law2<false>(m, lr, dcl_);
+    const float2 arg = __fmul2_rn(f2(kc), cl);
+    const float2 A = __fmul2_rn(wkk, make_float2(ex2_approx(arg.x), ex2_approx(arg.y)));
+    v[0] = __fmul2_rn(A, w0);
+    v[1] = __fmul2_rn(A, w1);
+    v[2] = __fmul2_rn(A, w2);
+    v[3] = __fmul2_rn(A, w3);
+}
+
 // The column-response build of ebuild with two consecutive band samples per
 // lane (k = k0 + 2 lane and k0 + 2 lane + 1, chunks of 64 strided by
 // `stride`): a lane whose two samples share their first tap column adds them
@@ -60,8 +135,24 @@ __device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *l
         const bool acta = ka <= kl, actb = kb <= kl;
         int fa = 0x40000000 + 2 * lane, fb = fa + 1;  // inactive: keys of their own, never written
         float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
-        if (acta) ebuild_point(m, lam, wk, ka, a, c, fa, va);
-        if (actb) ebuild_point(m, lam, wk, kb, a, c, fb, vb);
+        if (m.wnode) {  // node axis: binary searches, one band sample at a time
+            if (acta) ebuild_point(m, lam, wk, ka, a, c, fa, va);
+            if (actb) ebuild_point(m, lam, wk, kb, a, c, fb, vb);
+        } else if (acta) {
+            const int kb2 = actb ? kb : ka;
+            int f0, f1;
+            float2 v2[4];
+            ebuild_point2(m, make_float2(lam[ka], lam[kb2]), make_float2(wk[ka], wk[kb2]), a, kColour * c, f0, f1,
+                          v2);
+            fa = f0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) va[q] = v2[q].x;
+            if (actb) {
+                fb = f1;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) vb[q] = v2[q].y;
+            }
+        }
         const bool split = actb && fa != fb;  // (then acta as well)
         const int key = actb ? fb : fa;
         float v[4];
@@ -303,6 +394,72 @@ __device__ __forceinline__ void eadjoint(const ModelParams &m, const float *lam,
         const float Zs = -A * lr * a;  // d lambda'/dz = -lambda' a
         gc = fmaf(A * (kColourLn * cl), qs, gc);
         gz = fmaf(Zs, fmaf(kColourLn * c * dcl, qs, qd), gz);
+    }
+}
+
+// eadjoint with two band samples per lane, k and k + 32 of chunks of 64
+// strided by `stride`, through the packed FP32 instructions on the uniform
+// wavelength axis; each lane adds k's terms, then k + 32's, so with one warp
+// per sample (stride 64) the lane sums are those of eadjoint with stride 32.
+__device__ __forceinline__ void eadjoint_pair(const ModelParams &m, const float *lam, const float *wk, int kl,
+                                              int k_begin, int stride, float a, float c, int cc, int W, int lane,
+                                              const float *Q, int qstride, float &gc, float &gz) {
+    if (m.wnode) {  // node axis: one band sample at a time
+        for (int k0 = k_begin; k0 <= kl; k0 += stride) {
+            eadjoint(m, lam, wk, min(kl, k0 + 31), k0, 64, a, c, cc, W, lane, Q, qstride, gc, gz);
+            eadjoint(m, lam, wk, min(kl, k0 + 63), k0 + 32, 64, a, c, cc, W, lane, Q, qstride, gc, gz);
+        }
+        return;
+    }
+    const int NW = m.n_wave;
+    const float kc = kColour * c, kcl = kColourLn * c;
+    for (int k0 = k_begin; k0 <= kl; k0 += stride) {
+        const int ka = k0 + lane, kb = ka + 32;
+        if (ka > kl) continue;
+        const bool actb = kb <= kl;
+        const int kb2 = actb ? kb : ka;
+        const float2 lr = __fmul2_rn(make_float2(lam[ka], lam[kb2]), f2(a));
+        int ia, ib;
+        const float2 t = wave_locate2(m, lr, ia, ib);
+        const int fa = first_tap(ia, NW), fb = first_tap(ib, NW);
+        float2 qv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ca = fa + q - cc, cb = fb + q - cc;
+            qv[q] = make_float2((ca >= 0 && ca < W) ? Q[ca * qstride] : 0.f, (cb >= 0 && cb < W) ? Q[cb * qstride] : 0.f);
+        }
+        // Catmull-Rom coefficients (interior) or the straight line (edge interval), per half
+        float2 c0 = qv[1];
+        float2 c1 = __fmul2_rn(f2(0.5f), __fadd2_rn(qv[2], make_float2(-qv[0].x, -qv[0].y)));
+        float2 c2 = __ffma2_rn(f2(-0.5f), qv[3], __ffma2_rn(f2(2.0f), qv[2], __ffma2_rn(f2(-2.5f), qv[1], qv[0])));
+        float2 c3 = __ffma2_rn(f2(0.5f), __fadd2_rn(qv[3], make_float2(-qv[0].x, -qv[0].y)),
+                               __fmul2_rn(f2(1.5f), __fadd2_rn(qv[1], make_float2(-qv[2].x, -qv[2].y))));
+        const bool loa = ia == 0, hia = ia == NW - 2, lob = ib == 0, hib = ib == NW - 2;
+        if (loa || hia) {
+            const float p0 = loa ? qv[0].x : qv[2].x, p1 = loa ? qv[1].x : qv[3].x;
+            c0.x = p0; c1.x = p1 - p0; c2.x = 0.f; c3.x = 0.f;
+        }
+        if (lob || hib) {
+            const float p0 = lob ? qv[0].y : qv[2].y, p1 = lob ? qv[1].y : qv[3].y;
+            c0.y = p0; c1.y = p1 - p0; c2.y = 0.f; c3.y = 0.f;
+        }
+        const float2 qs = __ffma2_rn(__ffma2_rn(__ffma2_rn(c3, t, c2), t, c1), t, c0);
+        const float2 iw = f2(m.inv_dwave);
+        const float2 qd =
+            __fmul2_rn(__ffma2_rn(__ffma2_rn(__fmul2_rn(f2(3.0f), c3), t, __fmul2_rn(f2(2.0f), c2)), t, c1), iw);
+        float2 dcl;
+        const float2 cl = colour_law2<true>(m, lr, dcl);
+        const float2 arg = __fmul2_rn(f2(kc), cl);
+        const float2 A = __fmul2_rn(make_float2(wk[ka], wk[kb2]), make_float2(ex2_approx(arg.x), ex2_approx(arg.y)));
+        const float2 Zs = __fmul2_rn(__fmul2_rn(make_float2(-A.x, -A.y), lr), f2(a));
+        const float2 Ac = __fmul2_rn(A, __fmul2_rn(f2(kColourLn), cl));
+        const float2 Zt = __ffma2_rn(__fmul2_rn(f2(kcl), dcl), qs, qd);
+        gc = fmaf(Ac.x, qs.x, gc);
+        gz = fmaf(Zs.x, Zt.x, gz);
+        if (actb) {
+            gc = fmaf(Ac.y, qs.y, gc);
+            gz = fmaf(Zs.y, Zt.y, gz);
+        }
     }
 }
 

@@ -73,10 +73,15 @@ struct Lay {
 enum { PJ_A = 0, PJ_X0, PJ_X1, PJ_C, PJ_OK, PJ_KF, PJ_KL, PJ_NUM };
 
 // Row dot of one touched row against the column responses of the tile:
-// acc[j] += sum_col G[row][col] E[col][j] over this lane's columns.
+// acc[j] += sum_col G[row][col] E[col][j] over this lane's columns. For an
+// even tile the samples go in pairs through the packed FP32 FMA (acc[p] holds
+// samples 2p and 2p + 1; the grid value is broadcast to both halves): per
+// column and pair one instruction per surface instead of two. Each half is
+// an ordinary fused multiply-add, so the sums are those of the scalar loop.
 template <int TJ, bool SMEM>
-__device__ __forceinline__ void fwd_row_dot(const float2 *grow, int W, int l4, const float *sE, float *acc0,
-                                            float *acc1) {
+__device__ __forceinline__ void fwd_row_dot(const float2 *grow, int W, int l4, const float *sE, float2 *acc0,
+                                            float2 *acc1) {
+    static_assert(TJ % 2 == 0, "packed row dot needs an even tile");
     constexpr int U = 8;
     for (int col0 = l4; col0 < W; col0 += U * LPR) {
         float2 gv[U];
@@ -88,33 +93,61 @@ __device__ __forceinline__ void fwd_row_dot(const float2 *grow, int W, int l4, c
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int col = min(col0 + u * LPR, W - 1);
-            const float *ev = sE + col * TJ;
+            const float2 gx = make_float2(gv[u].x, gv[u].x), gy = make_float2(gv[u].y, gv[u].y);
             if (TJ % 4 == 0) {
+                const float4 *ev = reinterpret_cast<const float4 *>(sE + col * TJ);
 #pragma unroll
-                for (int j = 0; j < TJ; j += 4) {
-                    const float4 e4 = *reinterpret_cast<const float4 *>(ev + j);
-                    acc0[j] = fmaf(gv[u].x, e4.x, acc0[j]); acc1[j] = fmaf(gv[u].y, e4.x, acc1[j]);
-                    acc0[j + 1] = fmaf(gv[u].x, e4.y, acc0[j + 1]); acc1[j + 1] = fmaf(gv[u].y, e4.y, acc1[j + 1]);
-                    acc0[j + 2] = fmaf(gv[u].x, e4.z, acc0[j + 2]); acc1[j + 2] = fmaf(gv[u].y, e4.z, acc1[j + 2]);
-                    acc0[j + 3] = fmaf(gv[u].x, e4.w, acc0[j + 3]); acc1[j + 3] = fmaf(gv[u].y, e4.w, acc1[j + 3]);
+                for (int p4 = 0; p4 < TJ / 4; ++p4) {
+                    const float4 e4 = ev[p4];
+                    const float2 ea = make_float2(e4.x, e4.y), eb = make_float2(e4.z, e4.w);
+                    acc0[2 * p4] = __ffma2_rn(gx, ea, acc0[2 * p4]);
+                    acc1[2 * p4] = __ffma2_rn(gy, ea, acc1[2 * p4]);
+                    acc0[2 * p4 + 1] = __ffma2_rn(gx, eb, acc0[2 * p4 + 1]);
+                    acc1[2 * p4 + 1] = __ffma2_rn(gy, eb, acc1[2 * p4 + 1]);
                 }
             } else {
+                const float2 *ev = reinterpret_cast<const float2 *>(sE + col * TJ);
 #pragma unroll
-                for (int j = 0; j < TJ; ++j) {
-                    acc0[j] = fmaf(gv[u].x, ev[j], acc0[j]);
-                    acc1[j] = fmaf(gv[u].y, ev[j], acc1[j]);
+                for (int p = 0; p < TJ / 2; ++p) {
+                    const float2 e = ev[p];
+                    acc0[p] = __ffma2_rn(gx, e, acc0[p]);
+                    acc1[p] = __ffma2_rn(gy, e, acc1[p]);
                 }
             }
         }
     }
 }
 
+// The same for a one-sample tile (scalar FMAs).
+template <bool SMEM>
+__device__ __forceinline__ void fwd_row_dot1(const float2 *grow, int W, int l4, const float *sE, float &acc0,
+                                             float &acc1) {
+    constexpr int U = 8;
+    for (int col0 = l4; col0 < W; col0 += U * LPR) {
+        float2 gv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int col = col0 + u * LPR;
+            gv[u] = col < W ? (SMEM ? grow[col] : __ldg(grow + col)) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float e = sE[min(col0 + u * LPR, W - 1)];
+            acc0 = fmaf(gv[u].x, e, acc0);
+            acc1 = fmaf(gv[u].y, e, acc1);
+        }
+    }
+}
+
 // Back-projection of the adjoint rows onto one column, over the rows
-// rs, rs + nrs, ...: q[j] += sum_r Y[r][j] G[r][col]. With SMEM the grid rows
-// are the staged window's slots (slot = position in the touched-row list).
+// rs, rs + nrs, ...: q[j] += sum_r Y[r][j] G[r][col], samples in pairs
+// through the packed FMA as in fwd_row_dot (q[p] holds samples 2p, 2p + 1).
+// With SMEM the grid rows are the staged window's slots (slot = position in
+// the touched-row list).
 template <int TJ, bool SMEM>
 __device__ __forceinline__ void rev_col_dot(const float2 *gcol, size_t stride, const int *sRows, int rs, int nrs,
-                                            int nrows, const float *sY, float *q0, float *q1) {
+                                            int nrows, const float *sY, float2 *q0, float2 *q1) {
+    static_assert(TJ % 2 == 0, "packed column dot needs an even tile");
     constexpr int U = 8;
     for (int rr0 = rs; rr0 < nrows; rr0 += U * nrs) {
         float2 gv[U];
@@ -129,12 +162,52 @@ __device__ __forceinline__ void rev_col_dot(const float2 *gcol, size_t stride, c
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (rv[u] < 0) continue;
-            const float *yv = sY + rv[u] * TJ;
+            const float2 gx = make_float2(gv[u].x, gv[u].x), gy = make_float2(gv[u].y, gv[u].y);
+            if (TJ % 4 == 0) {
+                const float4 *yv = reinterpret_cast<const float4 *>(sY + rv[u] * TJ);
 #pragma unroll
-            for (int j = 0; j < TJ; ++j) {
-                q0[j] = fmaf(yv[j], gv[u].x, q0[j]);
-                q1[j] = fmaf(yv[j], gv[u].y, q1[j]);
+                for (int p4 = 0; p4 < TJ / 4; ++p4) {
+                    const float4 y4 = yv[p4];
+                    const float2 ya = make_float2(y4.x, y4.y), yb = make_float2(y4.z, y4.w);
+                    q0[2 * p4] = __ffma2_rn(ya, gx, q0[2 * p4]);
+                    q1[2 * p4] = __ffma2_rn(ya, gy, q1[2 * p4]);
+                    q0[2 * p4 + 1] = __ffma2_rn(yb, gx, q0[2 * p4 + 1]);
+                    q1[2 * p4 + 1] = __ffma2_rn(yb, gy, q1[2 * p4 + 1]);
+                }
+            } else {
+                const float2 *yv = reinterpret_cast<const float2 *>(sY + rv[u] * TJ);
+#pragma unroll
+                for (int p = 0; p < TJ / 2; ++p) {
+                    const float2 y = yv[p];
+                    q0[p] = __ffma2_rn(y, gx, q0[p]);
+                    q1[p] = __ffma2_rn(y, gy, q1[p]);
+                }
             }
+        }
+    }
+}
+
+// The same for a one-sample tile.
+template <bool SMEM>
+__device__ __forceinline__ void rev_col_dot1(const float2 *gcol, size_t stride, const int *sRows, int rs, int nrs,
+                                             int nrows, const float *sY, float &q0, float &q1) {
+    constexpr int U = 8;
+    for (int rr0 = rs; rr0 < nrows; rr0 += U * nrs) {
+        float2 gv[U];
+        int rv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int rr = rr0 + u * nrs;
+            rv[u] = rr < nrows ? sRows[rr] : -1;
+            gv[u] = rv[u] < 0 ? make_float2(0.f, 0.f)
+                              : (SMEM ? gcol[(size_t)rr * stride] : __ldg(gcol + (size_t)rv[u] * stride));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (rv[u] < 0) continue;
+            const float y = sY[rv[u]];
+            q0 = fmaf(y, gv[u].x, q0);
+            q1 = fmaf(y, gv[u].y, q1);
         }
     }
 }
@@ -431,11 +504,26 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 const int rr = rbase + warp * RPW + lane / LPR;
                                 const bool valid = rr < nrows;
                                 const int r = valid ? sRows[rr] : 0;
-                                float acc0[TJ], acc1[TJ];
+                                float acc0[TJ], acc1[TJ];  // per sample: M0 and M1 row dots
+                                if constexpr (TJ == 1) {
+                                    acc0[0] = 0.f; acc1[0] = 0.f;
+                                    if (valid)
+                                        fwd_row_dot1<false>(m.g01 + (size_t)r * m.nw_pitch + cc, W, l4, sE, acc0[0],
+                                                            acc1[0]);
+                                } else {
+                                    float2 a0[TJ / 2], a1[TJ / 2];
 #pragma unroll
-                                for (int j = 0; j < TJ; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
-                                if (valid)
-                                    fwd_row_dot<TJ, false>(m.g01 + (size_t)r * m.nw_pitch + cc, W, l4, sE, acc0, acc1);
+                                    for (int p = 0; p < TJ / 2; ++p) {
+                                        a0[p] = make_float2(0.f, 0.f); a1[p] = make_float2(0.f, 0.f);
+                                    }
+                                    if (valid)
+                                        fwd_row_dot<TJ, false>(m.g01 + (size_t)r * m.nw_pitch + cc, W, l4, sE, a0, a1);
+#pragma unroll
+                                    for (int p = 0; p < TJ / 2; ++p) {
+                                        acc0[2 * p] = a0[p].x; acc0[2 * p + 1] = a0[p].y;
+                                        acc1[2 * p] = a1[p].x; acc1[2 * p + 1] = a1[p].y;
+                                    }
+                                }
 #pragma unroll
                                 for (int sh = 1; sh < LPR; sh <<= 1) {
 #pragma unroll
@@ -574,14 +662,26 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             const int nrs = THREADS / Wp;
                             {
                                 const int col = tid % Wp, rs = tid / Wp;
-                                float q0[TJ], q1[TJ];
+                                if constexpr (TJ == 1) {
+                                    float q0 = 0.f, q1 = 0.f;
+                                    if (col < W && rs < nrs)
+                                        rev_col_dot1<false>(m.g01 + cc + col, (size_t)m.nw_pitch, sRows, rs, nrs,
+                                                            nrows, sY, q0, q1);
+                                    sQ[tid] = fmaf(sPj[PJ_X1], q1, q0);
+                                } else {
+                                    float2 q0[TJ / 2], q1[TJ / 2];
 #pragma unroll
-                                for (int j = 0; j < TJ; ++j) { q0[j] = 0.f; q1[j] = 0.f; }
-                                if (col < W && rs < nrs)
-                                    rev_col_dot<TJ, false>(m.g01 + cc + col, (size_t)m.nw_pitch, sRows, rs, nrs, nrows,
-                                                           sY, q0, q1);
+                                    for (int p = 0; p < TJ / 2; ++p) {
+                                        q0[p] = make_float2(0.f, 0.f); q1[p] = make_float2(0.f, 0.f);
+                                    }
+                                    if (col < W && rs < nrs)
+                                        rev_col_dot<TJ, false>(m.g01 + cc + col, (size_t)m.nw_pitch, sRows, rs, nrs,
+                                                               nrows, sY, q0, q1);
+                                    const float2 *x1p = reinterpret_cast<const float2 *>(sPj + PJ_X1 * TJ);
+                                    float2 *qo = reinterpret_cast<float2 *>(sQ + tid * TJ);
 #pragma unroll
-                                for (int j = 0; j < TJ; ++j) sQ[tid * TJ + j] = fmaf(sPj[PJ_X1 * TJ + j], q1[j], q0[j]);
+                                    for (int p = 0; p < TJ / 2; ++p) qo[p] = __ffma2_rn(x1p[p], q1[p], q0[p]);
+                                }
                             }
                             __syncthreads();
                             // Q[col][j] = sum over row subsets in order (into the E buffer, free now)
@@ -602,7 +702,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
                                     const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                     const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
-                                    eadjoint(m, lam, wk, kl, kf + 32 * sub, 32 * WPS, a, c, cc, W, lane, sQf + j, TJ,
+                                    eadjoint_pair(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, sQf + j, TJ,
                                              gacc[jj][4], gacc[jj][5]);
                                 }
                             }
