@@ -109,6 +109,57 @@ __device__ __forceinline__ void axis_taps(float x, float x0, float inv_dx, float
     axis_taps_from<DERIV>(i, t, n, inv_dx, tp);
 }
 
+// ---- Packed FP32 (fma/mul/add .f32x2) forms of the tap arithmetic: two
+// coordinates at once, each half the IEEE operation of the scalar code.
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+// a - b, exactly rounded as the scalar subtraction
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// keys_weights on both halves.
+__device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4]) {
+    const float2 t2 = __fmul2_rn(t, t);
+    w[0] = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(f2(-0.5f), t, f2(1.0f)), f2(-0.5f)));
+    w[1] = __ffma2_rn(t2, __ffma2_rn(f2(1.5f), t, f2(-2.5f)), f2(1.0f));
+    w[2] = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(f2(-1.5f), t, f2(2.0f)), f2(0.5f)));
+    w[3] = __fmul2_rn(t2, __ffma2_rn(f2(0.5f), t, f2(-0.5f)));
+}
+
+// keys_dweights on both halves.
+__device__ __forceinline__ void keys_dweights2(float2 t, float2 (&d)[4]) {
+    d[0] = __ffma2_rn(t, __ffma2_rn(f2(-1.5f), t, f2(2.0f)), f2(-0.5f));
+    d[1] = __fmul2_rn(t, __ffma2_rn(f2(4.5f), t, f2(-5.0f)));
+    d[2] = __ffma2_rn(t, __ffma2_rn(f2(-4.5f), t, f2(4.0f)), f2(0.5f));
+    d[3] = __fmul2_rn(t, __ffma2_rn(f2(1.5f), t, f2(-1.0f)));
+}
+
+// Taps of two located intervals (ia, t.x) and (ib, t.y) on an axis of n
+// nodes, inverse widths iw: axis_taps_from on each half.
+template <bool DERIV>
+__device__ __forceinline__ void axis_taps_from2(int ia, int ib, float2 t, int n, float2 iw, int &fa, int &fb,
+                                                float2 (&w)[4], float2 (&dw)[4]) {
+    const bool ea = ia == 0 || ia == n - 2, eb = ib == 0 || ib == n - 2, la = ia == 0, lb = ib == 0;
+    fa = ea ? (la ? 0 : n - 4) : ia - 1;
+    fb = eb ? (lb ? 0 : n - 4) : ib - 1;
+    float2 kw[4];
+    keys_weights2(t, kw);
+    const float2 l0 = fsub2(f2(1.0f), t);
+    w[0] = make_float2(ea ? (la ? l0.x : 0.f) : kw[0].x, eb ? (lb ? l0.y : 0.f) : kw[0].y);
+    w[1] = make_float2(ea ? (la ? t.x : 0.f) : kw[1].x, eb ? (lb ? t.y : 0.f) : kw[1].y);
+    w[2] = make_float2(ea ? (la ? 0.f : l0.x) : kw[2].x, eb ? (lb ? 0.f : l0.y) : kw[2].y);
+    w[3] = make_float2(ea ? (la ? 0.f : t.x) : kw[3].x, eb ? (lb ? 0.f : t.y) : kw[3].y);
+    if (DERIV) {
+        float2 kd[4];
+        keys_dweights2(t, kd);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) kd[q] = __fmul2_rn(kd[q], iw);
+        dw[0] = make_float2(ea ? (la ? -iw.x : 0.f) : kd[0].x, eb ? (lb ? -iw.y : 0.f) : kd[0].y);
+        dw[1] = make_float2(ea ? (la ? iw.x : 0.f) : kd[1].x, eb ? (lb ? iw.y : 0.f) : kd[1].y);
+        dw[2] = make_float2(ea ? (la ? 0.f : -iw.x) : kd[2].x, eb ? (lb ? 0.f : -iw.y) : kd[2].y);
+        dw[3] = make_float2(ea ? (la ? 0.f : iw.x) : kd[3].x, eb ? (lb ? 0.f : iw.y) : kd[3].y);
+    }
+}
+
 // ---- The phase coordinate as a float pair.
 // The rest-frame phase (mjd - t0) / (1 + z) is a difference of epochs ~5e4 d
 // apart by tens of days. Formed in FP32, the phase (or its grid coordinate
@@ -188,6 +239,38 @@ __device__ __forceinline__ bool phase_find(const ModelParams &m, float2 tm, floa
     t = fminf((__fadd_rn(u.x, -__ldg(m.pnode + lo)) + (u.y - __ldg(m.pnode_lo + lo))) * iw, 1.0f);
     p = u.x;
     return true;
+}
+
+// phase_find for two observation times under one phase map: on a uniform
+// axis the float-pair arithmetic of phase_u runs on both halves at once; on a
+// node axis it is phase_find twice. oka / okb say whether each phase is on
+// the axis (ia, ib, t, iw, p are then set for that half).
+__device__ __forceinline__ void phase_find2(const ModelParams &m, float2 tma, float2 tmb, float4 pm, bool &oka,
+                                            bool &okb, int &ia, int &ib, float2 &t, float2 &iw, float2 &p) {
+    if (m.pnode) {
+        oka = phase_find(m, tma, pm, ia, t.x, iw.x, p.x);
+        okb = phase_find(m, tmb, pm, ib, t.y, iw.y, p.y);
+        return;
+    }
+    const float2 th = make_float2(tma.x, tmb.x), tl = make_float2(tma.y, tmb.y);
+    const float2 dh = __fadd2_rn(th, f2(-pm.x));  // two-sum of the hi parts and -O.x
+    const float2 bv = fsub2(dh, th);
+    const float2 de = fsub2(fsub2(th, fsub2(dh, bv)), __fadd2_rn(f2(pm.x), bv));
+    const float2 dl = __fadd2_rn(de, __fadd2_rn(tl, f2(-pm.y)));
+    const float2 uh = __fmul2_rn(dh, f2(pm.z));
+    float2 ue = __ffma2_rn(dh, f2(pm.z), make_float2(-uh.x, -uh.y));
+    ue = __ffma2_rn(dh, f2(pm.w), ue);
+    ue = __ffma2_rn(dl, f2(pm.z), ue);
+    const float2 s = __fadd2_rn(uh, ue);
+    const float2 e = fsub2(ue, fsub2(s, uh));
+    const float top = (float)(m.n_phase - 1);
+    oka = (s.x > 0.f || (s.x == 0.f && e.x >= 0.f)) && (s.x < top || (s.x == top && e.x <= 0.f));
+    okb = (s.y > 0.f || (s.y == 0.f && e.y >= 0.f)) && (s.y < top || (s.y == top && e.y <= 0.f));
+    ia = min(max(__float2int_rd(s.x), 0), m.n_phase - 2);
+    ib = min(max(__float2int_rd(s.y), 0), m.n_phase - 2);
+    t = __fadd2_rn(__fadd2_rn(s, make_float2(-(float)ia, -(float)ib)), e);
+    iw = f2(m.inv_dphase);
+    p = __ffma2_rn(s, f2(m.dphase), f2(m.phase0));
 }
 
 __device__ __forceinline__ bool wave_find(const ModelParams &m, float lam, int &i, float &t, float &iw) {

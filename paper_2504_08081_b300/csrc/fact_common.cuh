@@ -48,17 +48,6 @@ __device__ __forceinline__ void ebuild_point(const ModelParams &m, const float *
 // (fma/mul/add .f32x2): each half is the IEEE operation of the scalar code,
 // in the same order, so the values are those of one band sample at a time.
 
-__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
-
-// keys_weights on both halves.
-__device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4]) {
-    const float2 t2 = __fmul2_rn(t, t);
-    w[0] = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(f2(-0.5f), t, f2(1.0f)), f2(-0.5f)));
-    w[1] = __ffma2_rn(t2, __ffma2_rn(f2(1.5f), t, f2(-2.5f)), f2(1.0f));
-    w[2] = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(f2(-1.5f), t, f2(2.0f)), f2(0.5f)));
-    w[3] = __fmul2_rn(t2, __ffma2_rn(f2(0.5f), t, f2(-0.5f)));
-}
-
 // colour_law on both halves (value; with DERIV also dCL/dlambda).
 template <bool DERIV>
 __device__ __forceinline__ float2 colour_law2(const ModelParams &m, float2 lam, float2 &dcl) {

@@ -212,6 +212,40 @@ __device__ __forceinline__ void rev_col_dot1(const float2 *gcol, size_t stride, 
     }
 }
 
+// Y[first + m] += v_m for the 4 taps of each lane (first < 0: nothing).
+// Lanes with the same first row form one group for all 4 taps; each group's
+// sums run in lane order (deterministic) and its lowest lane adds them, tap
+// by tap, so groups whose rows overlap add in a fixed order too. yval: 32
+// float4 of the warp's staging.
+__device__ __forceinline__ void y_scatter(float *yw, float *yval, int lane, int first, float4 yv) {
+    const bool has = first >= 0;
+    const int key = has ? first : -1 - lane;
+    if (!has) yv = make_float4(0.f, 0.f, 0.f, 0.f);
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const bool lead = has && lane == __ffs(grp) - 1;
+    if (!__all_sync(0xffffffffu, grp == (1u << lane))) {
+        reinterpret_cast<float4 *>(yval)[lane] = yv;
+        __syncwarp();
+        if (lead) {
+            float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned g2 = grp;
+            while (g2) {
+                const float4 v = reinterpret_cast<const float4 *>(yval)[__ffs(g2) - 1];
+                s4.x += v.x; s4.y += v.y; s4.z += v.z; s4.w += v.w;
+                g2 &= g2 - 1;
+            }
+            yv = s4;
+        }
+        __syncwarp();
+    }
+    const float ys[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) {
+        if (lead) yw[key + mm] += ys[mm];
+        __syncwarp();
+    }
+}
+
 template <int TJ, int MODE>
 __global__ void __launch_bounds__(THREADS, 3)
 k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items,
@@ -557,85 +591,80 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             const float x1 = sPj[PJ_X1 * TJ + j];
                             const float4 pm = sPm[j];
                             float *yw = sYw + (warp * SPW + jj) * NP;
-                            for (int base = sub * 32; base < nb_obs; base += 32 * WPS) {
-                                const int il = base + lane;
-                                const bool act = il < nb_obs;
-                                Taps4 tp;
-                                tp.first = -1;
-                                float Bs = 0.f, Bp = 0.f, B1 = 0.f, coef = 0.f;
-                                if (act) {
-                                    const int i = ordb[il];
-                                    int iv; float t, iwp, p = 0.f;
-                                    if (okj && phase_find(m, sMjd[i], pm, iv, t, iwp, p)) {
-                                        axis_taps_from<GRAD>(iv, t, NP, iwp, tp);
+                            // observations in pairs (il, il + 32) through the packed FP32 forms; each
+                            // lane takes il's terms, then il + 32's (the order of the one-at-a-time loop)
+                            for (int base = sub * 64; base < nb_obs; base += 64 * WPS) {
+                                const int ila = base + lane, ilb = ila + 32;
+                                const bool acta = ila < nb_obs, actb = ilb < nb_obs;
+                                const int ia = ordb[acta ? ila : 0], ib = ordb[actb ? ilb : 0];
+                                bool oka = false, okb = false;
+                                int iva = 0, ivb = 0;
+                                float2 t = f2(0.f), iwp = f2(0.f), p = f2(0.f);
+                                if (okj && acta) phase_find2(m, sMjd[ia], sMjd[ib], pm, oka, okb, iva, ivb, t, iwp, p);
+                                oka = oka && acta;
+                                okb = okb && actb;
+                                t = make_float2(oka ? t.x : 0.f, okb ? t.y : 0.f);  // finite weights off the axis
+                                int fa, fb;
+                                float2 w[4], dw[4];
+                                axis_taps_from2<GRAD>(iva, ivb, t, NP, iwp, fa, fb, w, dw);
+                                if (!oka) fa = -1;
+                                if (!okb) fb = -1;
+                                float2 Bs = f2(0.f), Bp = f2(0.f), B1 = f2(0.f);
+                                const float *dj = sD + j * NP * 2;
 #pragma unroll
-                                        for (int mm = 0; mm < 4; ++mm) {
-                                            const float2 dv = *reinterpret_cast<const float2 *>(sD + (j * NP + tp.first + mm) * 2);
-                                            const float h = fmaf(x1, dv.y, dv.x);
-                                            Bs = fmaf(tp.w[mm], h, Bs);
-                                            if (GRAD) {
-                                                Bp = fmaf(tp.dw[mm], h, Bp);
-                                                B1 = fmaf(tp.w[mm], dv.y, B1);
-                                            }
-                                        }
-                                    } else {
-                                        tp.first = -1;
+                                for (int mm = 0; mm < 4; ++mm) {
+                                    const float2 da = oka ? *reinterpret_cast<const float2 *>(dj + (fa + mm) * 2) : f2(0.f);
+                                    const float2 db = okb ? *reinterpret_cast<const float2 *>(dj + (fb + mm) * 2) : f2(0.f);
+                                    const float2 dy = make_float2(da.y, db.y);
+                                    const float2 h = __ffma2_rn(f2(x1), dy, make_float2(da.x, db.x));
+                                    Bs = __ffma2_rn(w[mm], h, Bs);
+                                    if (GRAD) {
+                                        Bp = __ffma2_rn(dw[mm], h, Bp);
+                                        B1 = __ffma2_rn(w[mm], dy, B1);
                                     }
-                                    const float zpf = sZpf[i];
-                                    const float pre = x0 * a * zpf;
-                                    const float B = pre * Bs;
-                                    if (!isfinite(B)) atomicOr(o.err, ERRBIT_RANGE);
+                                }
+                                float2 coef = f2(0.f);
+                                if (acta) {
+                                    const float2 zpf = make_float2(sZpf[ia], sZpf[ib]);
+                                    const float2 pre = __fmul2_rn(f2(x0 * a), zpf);
+                                    const float2 B = __fmul2_rn(pre, Bs);
+                                    if (!isfinite(B.x) || (actb && !isfinite(B.y))) atomicOr(o.err, ERRBIT_RANGE);
                                     if (MODE == MODE_BANDFLUX) {
-                                        o.bandflux[wi.bf0 + (int64_t)(jloc0 + j) * nobs + (oc + i)] = B;
+                                        float *bo = o.bandflux + wi.bf0 + (int64_t)(jloc0 + j) * nobs + oc;
+                                        bo[ia] = B.x;
+                                        if (actb) bo[ib] = B.y;
                                     } else {
-                                        const float isig = sSig[i];
-                                        const float r = (sFlux[i] - B) * isig;
-                                        chi_acc[jj] = fma((double)r, (double)r, chi_acc[jj]);
+                                        const float2 isig = make_float2(sSig[ia], sSig[ib]);
+                                        const float2 r = __fmul2_rn(fsub2(make_float2(sFlux[ia], sFlux[ib]), B), isig);
+                                        chi_acc[jj] = fma((double)r.x, (double)r.x, chi_acc[jj]);
+                                        if (actb) chi_acc[jj] = fma((double)r.y, (double)r.y, chi_acc[jj]);
                                         if (GRAD) {
-                                            const float g = -2.0f * r * isig;
-                                            gacc[jj][0] += g * (-a * B - pre * a * p * Bp);
-                                            gacc[jj][1] += g * pre * Bp * (-a);
-                                            gacc[jj][2] += g * a * zpf * Bs;
-                                            gacc[jj][3] += g * pre * B1;
-                                            coef = g * pre;
+                                            const float2 g = __fmul2_rn(__fmul2_rn(f2(-2.0f), r), isig);
+                                            // terms of dchi2/dz (prefactor and phase), dt0, dx0, dx1
+                                            const float2 T0 = fsub2(__fmul2_rn(f2(-a), B),
+                                                                    __fmul2_rn(__fmul2_rn(__fmul2_rn(pre, f2(a)), p), Bp));
+                                            const float2 T1 = __fmul2_rn(__fmul2_rn(pre, Bp), f2(-a));
+                                            const float2 T2 = __fmul2_rn(__fmul2_rn(f2(a), zpf), Bs);
+                                            const float2 T3 = __fmul2_rn(pre, B1);
+                                            gacc[jj][0] = fmaf(g.x, T0.x, gacc[jj][0]);
+                                            gacc[jj][1] = fmaf(g.x, T1.x, gacc[jj][1]);
+                                            gacc[jj][2] = fmaf(g.x, T2.x, gacc[jj][2]);
+                                            gacc[jj][3] = fmaf(g.x, T3.x, gacc[jj][3]);
+                                            if (actb) {
+                                                gacc[jj][0] = fmaf(g.y, T0.y, gacc[jj][0]);
+                                                gacc[jj][1] = fmaf(g.y, T1.y, gacc[jj][1]);
+                                                gacc[jj][2] = fmaf(g.y, T2.y, gacc[jj][2]);
+                                                gacc[jj][3] = fmaf(g.y, T3.y, gacc[jj][3]);
+                                            }
+                                            coef = __fmul2_rn(g, pre);
                                         }
                                     }
                                 }
                                 if (GRAD) {
-                                    // Y[first + m] += coef * phi_m for the 4 taps. Lanes with the
-                                    // same first row form one group for all 4 taps; each group's
-                                    // sums run in lane order (deterministic) and its lowest lane
-                                    // adds them, tap by tap, so groups whose rows overlap add in
-                                    // a fixed order too.
-                                    const bool has = tp.first >= 0;
-                                    const int key = has ? tp.first : -1 - lane;
-                                    float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-                                    if (has)
-                                        yv = make_float4(coef * tp.w[0], coef * tp.w[1], coef * tp.w[2],
-                                                         coef * tp.w[3]);
-                                    const unsigned grp = __match_any_sync(0xffffffffu, key);
-                                    const bool lead = has && lane == __ffs(grp) - 1;
-                                    if (!__all_sync(0xffffffffu, grp == (1u << lane))) {
-                                        reinterpret_cast<float4 *>(yval)[lane] = yv;
-                                        __syncwarp();
-                                        if (lead) {
-                                            float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                                            unsigned g2 = grp;
-                                            while (g2) {
-                                                const float4 v = reinterpret_cast<const float4 *>(yval)[__ffs(g2) - 1];
-                                                s4.x += v.x; s4.y += v.y; s4.z += v.z; s4.w += v.w;
-                                                g2 &= g2 - 1;
-                                            }
-                                            yv = s4;
-                                        }
-                                        __syncwarp();
-                                    }
-                                    const float ys[4] = {yv.x, yv.y, yv.z, yv.w};
-#pragma unroll
-                                    for (int mm = 0; mm < 4; ++mm) {
-                                        if (lead) yw[key + mm] += ys[mm];
-                                        __syncwarp();
-                                    }
+                                    y_scatter(yw, yval, lane, fa,
+                                              make_float4(coef.x * w[0].x, coef.x * w[1].x, coef.x * w[2].x, coef.x * w[3].x));
+                                    y_scatter(yw, yval, lane, fb,
+                                              make_float4(coef.y * w[0].y, coef.y * w[1].y, coef.y * w[2].y, coef.y * w[3].y));
                                 }
                             }
                         }
