@@ -75,23 +75,27 @@ __device__ __forceinline__ bool axis_find(float x, float x0, float inv_dx, float
 // taps stay in registers.
 template <bool DERIV>
 __device__ __forceinline__ void axis_taps_from(int i, float t, int n, float inv_dx, Taps4 &tp) {
-    const bool edge = i == 0 || i == n - 2;
-    const bool lo = i == 0;  // first interval: linear weights on nodes 0, 1; last: on n-2, n-1
-    tp.first = edge ? (lo ? 0 : n - 4) : i - 1;
-    float kw[4];
-    keys_weights(t, kw);
-    const float l0 = 1.0f - t;
-    tp.w[0] = edge ? (lo ? l0 : 0.f) : kw[0];
-    tp.w[1] = edge ? (lo ? t : 0.f) : kw[1];
-    tp.w[2] = edge ? (lo ? 0.f : l0) : kw[2];
-    tp.w[3] = edge ? (lo ? 0.f : t) : kw[3];
+    tp.first = i - 1;
+    keys_weights(t, tp.w);
     if (DERIV) {
-        float kd[4];
-        keys_dweights(t, kd);
-        tp.dw[0] = edge ? (lo ? -inv_dx : 0.f) : kd[0] * inv_dx;
-        tp.dw[1] = edge ? (lo ? inv_dx : 0.f) : kd[1] * inv_dx;
-        tp.dw[2] = edge ? (lo ? 0.f : -inv_dx) : kd[2] * inv_dx;
-        tp.dw[3] = edge ? (lo ? 0.f : inv_dx) : kd[3] * inv_dx;
+        keys_dweights(t, tp.dw);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tp.dw[q] *= inv_dx;
+    }
+    if (i == 0 || i == n - 2) {  // first interval: linear weights on nodes 0, 1; last: on n-2, n-1
+        const bool lo = i == 0;
+        const float l0 = 1.0f - t;
+        tp.first = lo ? 0 : n - 4;
+        tp.w[0] = lo ? l0 : 0.f;
+        tp.w[1] = lo ? t : 0.f;
+        tp.w[2] = lo ? 0.f : l0;
+        tp.w[3] = lo ? 0.f : t;
+        if (DERIV) {
+            tp.dw[0] = lo ? -inv_dx : 0.f;
+            tp.dw[1] = lo ? inv_dx : 0.f;
+            tp.dw[2] = lo ? 0.f : -inv_dx;
+            tp.dw[3] = lo ? 0.f : inv_dx;
+        }
     }
 }
 
@@ -138,25 +142,35 @@ __device__ __forceinline__ void keys_dweights2(float2 t, float2 (&d)[4]) {
 template <bool DERIV>
 __device__ __forceinline__ void axis_taps_from2(int ia, int ib, float2 t, int n, float2 iw, int &fa, int &fb,
                                                 float2 (&w)[4], float2 (&dw)[4]) {
-    const bool ea = ia == 0 || ia == n - 2, eb = ib == 0 || ib == n - 2, la = ia == 0, lb = ib == 0;
-    fa = ea ? (la ? 0 : n - 4) : ia - 1;
-    fb = eb ? (lb ? 0 : n - 4) : ib - 1;
-    float2 kw[4];
-    keys_weights2(t, kw);
-    const float2 l0 = fsub2(f2(1.0f), t);
-    w[0] = make_float2(ea ? (la ? l0.x : 0.f) : kw[0].x, eb ? (lb ? l0.y : 0.f) : kw[0].y);
-    w[1] = make_float2(ea ? (la ? t.x : 0.f) : kw[1].x, eb ? (lb ? t.y : 0.f) : kw[1].y);
-    w[2] = make_float2(ea ? (la ? 0.f : l0.x) : kw[2].x, eb ? (lb ? 0.f : l0.y) : kw[2].y);
-    w[3] = make_float2(ea ? (la ? 0.f : t.x) : kw[3].x, eb ? (lb ? 0.f : t.y) : kw[3].y);
+    fa = ia - 1;
+    fb = ib - 1;
+    keys_weights2(t, w);
     if (DERIV) {
-        float2 kd[4];
-        keys_dweights2(t, kd);
+        keys_dweights2(t, dw);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) kd[q] = __fmul2_rn(kd[q], iw);
-        dw[0] = make_float2(ea ? (la ? -iw.x : 0.f) : kd[0].x, eb ? (lb ? -iw.y : 0.f) : kd[0].y);
-        dw[1] = make_float2(ea ? (la ? iw.x : 0.f) : kd[1].x, eb ? (lb ? iw.y : 0.f) : kd[1].y);
-        dw[2] = make_float2(ea ? (la ? 0.f : -iw.x) : kd[2].x, eb ? (lb ? 0.f : -iw.y) : kd[2].y);
-        dw[3] = make_float2(ea ? (la ? 0.f : iw.x) : kd[3].x, eb ? (lb ? 0.f : iw.y) : kd[3].y);
+        for (int q = 0; q < 4; ++q) dw[q] = __fmul2_rn(dw[q], iw);
+    }
+    const bool ea = ia == 0 || ia == n - 2, eb = ib == 0 || ib == n - 2;
+    if (ea || eb) {  // first / last interval: linear weights on its two nodes
+        const float2 l0 = fsub2(f2(1.0f), t);
+        if (ea) {
+            const bool lo = ia == 0;
+            fa = lo ? 0 : n - 4;
+            w[0].x = lo ? l0.x : 0.f; w[1].x = lo ? t.x : 0.f; w[2].x = lo ? 0.f : l0.x; w[3].x = lo ? 0.f : t.x;
+            if (DERIV) {
+                dw[0].x = lo ? -iw.x : 0.f; dw[1].x = lo ? iw.x : 0.f;
+                dw[2].x = lo ? 0.f : -iw.x; dw[3].x = lo ? 0.f : iw.x;
+            }
+        }
+        if (eb) {
+            const bool lo = ib == 0;
+            fb = lo ? 0 : n - 4;
+            w[0].y = lo ? l0.y : 0.f; w[1].y = lo ? t.y : 0.f; w[2].y = lo ? 0.f : l0.y; w[3].y = lo ? 0.f : t.y;
+            if (DERIV) {
+                dw[0].y = lo ? -iw.y : 0.f; dw[1].y = lo ? iw.y : 0.f;
+                dw[2].y = lo ? 0.f : -iw.y; dw[3].y = lo ? 0.f : iw.y;
+            }
+        }
     }
 }
 

@@ -88,24 +88,14 @@ __device__ __forceinline__ void ebuild_point2(const ModelParams &m, float2 lamk,
     const float2 lr = __fmul2_rn(lamk, f2(a));
     int ia, ib;
     const float2 t = wave_locate2(m, lr, ia, ib);
-    float2 kw[4];
-    keys_weights2(t, kw);
-    const float2 l0 = __ffma2_rn(t, f2(-1.0f), f2(1.0f));
-    const bool ea = ia == 0 || ia == NW - 2, eb = ib == 0 || ib == NW - 2, loa = ia == 0, lob = ib == 0;
-    fa = ea ? (loa ? 0 : NW - 4) : ia - 1;
-    fb = eb ? (lob ? 0 : NW - 4) : ib - 1;
-    const float2 w0 = make_float2(ea ? (loa ? l0.x : 0.f) : kw[0].x, eb ? (lob ? l0.y : 0.f) : kw[0].y);
-    const float2 w1 = make_float2(ea ? (loa ? t.x : 0.f) : kw[1].x, eb ? (lob ? t.y : 0.f) : kw[1].y);
-    const float2 w2 = make_float2(ea ? (loa ? 0.f : l0.x) : kw[2].x, eb ? (lob ? 0.f : l0.y) : kw[2].y);
-    const float2 w3 = make_float2(ea ? (loa ? 0.f : t.x) : kw[3].x, eb ? (lob ? 0.f : t.y) : kw[3].y);
+    float2 w[4], dw_[4];
+    axis_taps_from2<false>(ia, ib, t, NW, f2(0.f), fa, fb, w, dw_);
     float2 dcl_;
     const float2 cl = colour_law2<false>(m, lr, dcl_);
     const float2 arg = __fmul2_rn(f2(kc), cl);
     const float2 A = __fmul2_rn(wkk, make_float2(ex2_approx(arg.x), ex2_approx(arg.y)));
-    v[0] = __fmul2_rn(A, w0);
-    v[1] = __fmul2_rn(A, w1);
-    v[2] = __fmul2_rn(A, w2);
-    v[3] = __fmul2_rn(A, w3);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __fmul2_rn(A, w[q]);
 }
 
 // The column-response build of ebuild with two consecutive band samples per
