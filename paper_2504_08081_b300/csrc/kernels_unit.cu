@@ -27,19 +27,19 @@ using fk::al16;
 
 struct Lay {
     // No block-level staging: the band tables are read through L1. With the D
-    // rows sized by the model's phase nodes a block takes ~48 KB (71 nodes, one
+    // rows sized by the model's phase nodes a block takes ~44 KB (71 nodes, one
     // sample, gradient); registers hold the kernel at three blocks per SM, and
     // the rest of the SM's 256 KB of L1/shared memory serves as L1 for the grid.
     size_t warp0, warp_bytes, total;
     __host__ __device__ Lay(int ts, bool grad, int np) {
-        const int ne = grad ? 3 : 1;
+        const int nd = grad ? 4 : 1;
         size_t o = 0;
         warp0 = o;
         // per warp: obs cache (index, mjd, flux, sig, zpf), column responses
-        // [WMAXW][ts][E (, E_c, E_z, pad)], row dots D [np][ts][2 ne], row list [np]
+        // [WMAXW][ts][E (, E_c, E_z, pad)], row dots D [np][ts][nd], row list [np]
         // (np = the model's phase nodes, at most NPHW)
         warp_bytes = al16(4 * OBS_W) + al16(8 * OBS_W) + 3 * al16(4 * OBS_W) +
-                     al16(4 * (size_t)WMAXW * ts * (grad ? 4 : 1)) + al16(4 * (size_t)np * ts * 2 * ne) +
+                     al16(4 * (size_t)WMAXW * ts * (grad ? 4 : 1)) + al16(4 * (size_t)np * ts * nd) +
                      al16(4 * (size_t)np);
         o += WARPS * warp_bytes;
         total = o;
@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(THREADS, 3)
 k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, int n_items, int *counter,
        UnitScratch scr, const int *n_items_dev) {
     constexpr bool GRAD = MODE == MODE_GRAD;
-    constexpr int NE = GRAD ? 3 : 1;  // column responses per sample: E (, E_c, E_z)
-    constexpr int ND = 2 * NE;        // row dots per (row, sample): x surfaces M0, M1
+    // row dots per (row, sample), with H = M0 + x1 M1 formed per grid value:
+    // H.E (, M1.E, H.E_c, H.E_z)
+    constexpr int ND = GRAD ? 4 : 1;
     constexpr int NEP = GRAD ? 4 : 1; // column-response slots per (column, sample)
     extern __shared__ __align__(16) unsigned char smem[];
     const Lay L(TS, GRAD, m.n_phase);
@@ -365,18 +366,15 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 const int col = min(col0 + 4 * uu, W - 1);
 #pragma unroll
                                 for (int s = 0; s < TS; ++s) {
+                                    const float h = fmaf(px1[s], gv[uu].y, gv[uu].x);  // M0 + x1 M1
                                     if constexpr (GRAD) {
                                         const float4 ev = *reinterpret_cast<const float4 *>(E + (col * TS + s) * 4);
-                                        acc[s][0] = fmaf(gv[uu].x, ev.x, acc[s][0]);
+                                        acc[s][0] = fmaf(h, ev.x, acc[s][0]);
                                         acc[s][1] = fmaf(gv[uu].y, ev.x, acc[s][1]);
-                                        acc[s][2] = fmaf(gv[uu].x, ev.y, acc[s][2]);
-                                        acc[s][3] = fmaf(gv[uu].y, ev.y, acc[s][3]);
-                                        acc[s][4] = fmaf(gv[uu].x, ev.z, acc[s][4]);
-                                        acc[s][5] = fmaf(gv[uu].y, ev.z, acc[s][5]);
+                                        acc[s][2] = fmaf(h, ev.y, acc[s][2]);
+                                        acc[s][3] = fmaf(h, ev.z, acc[s][3]);
                                     } else {
-                                        const float ev = E[col * TS + s];
-                                        acc[s][0] = fmaf(gv[uu].x, ev, acc[s][0]);
-                                        acc[s][1] = fmaf(gv[uu].y, ev, acc[s][1]);
+                                        acc[s][0] = fmaf(h, E[col * TS + s], acc[s][0]);
                                     }
                                 }
                             }
@@ -419,13 +417,12 @@ k_unit(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
 #pragma unroll
                             for (int mm = 0; mm < 4; ++mm) {
                                 const float *dv = D + ((tp.first + mm) * TS + s) * ND;
-                                const float h = fmaf(px1[s], dv[1], dv[0]);
-                                Bs = fmaf(tp.w[mm], h, Bs);
+                                Bs = fmaf(tp.w[mm], dv[0], Bs);
                                 if (GRAD) {
-                                    Bp = fmaf(tp.dw[mm], h, Bp);
+                                    Bp = fmaf(tp.dw[mm], dv[0], Bp);
                                     B1 = fmaf(tp.w[mm], dv[1], B1);
-                                    Bc = fmaf(tp.w[mm], fmaf(px1[s], dv[3], dv[2]), Bc);
-                                    Bz = fmaf(tp.w[mm], fmaf(px1[s], dv[5], dv[4]), Bz);
+                                    Bc = fmaf(tp.w[mm], dv[2], Bc);
+                                    Bz = fmaf(tp.w[mm], dv[3], Bz);
                                 }
                             }
                         }
