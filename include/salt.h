@@ -408,10 +408,9 @@ int salt_nested(salt_ctx *ctx, const salt_batch *batch, const double *lower, con
  * than 128 phase nodes; salt_last_error gives the bytes needed. Each call
  * copies the HOST offsets (pageable memory, cudaMemcpyAsync) into the array
  * and clears the counters that must start at zero, on cuda_stream. With
- * batch->validate set it synchronises cuda_stream to read the verdict, and
- * returns SALT_ERR_INVALID, touching nothing, while cuda_stream is capturing.
+ * batch->validate set it synchronises cuda_stream to read the verdict.
  * The first call on each device looks the array's address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).
  * The array is shared by every call on that device in the process: two calls
  * whose executions overlap (different streams, threads or contexts on the same
  * device) race on it and give wrong results, so serialise them. */

@@ -153,12 +153,6 @@ extern "C" int salt_chi2_grad_noalloc(salt_ctx *ctx, const salt_batch *bt, doubl
     b.mjd = bt->mjd; b.band = bt->band; b.flux = bt->flux; b.fluxerr = bt->fluxerr; b.zp = bt->zp;
     b.t0 = bt->t0; b.z = bt->z; b.x0 = bt->x0; b.x1 = bt->x1; b.c = bt->c;
     if (bt->validate) {
-        // validation reads its verdict back with a stream synchronisation,
-        // which a capturing stream does not allow
-        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-        if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return fail_cuda(ctx, e, "capture query");
-        if (cap != cudaStreamCaptureStatusNone)
-            return fail(ctx, SALT_ERR_INVALID, "validate synchronises the stream: not allowed while it is capturing");
         int flag = 0;
         e = cudaMemsetAsync(ctx->err_d + 1, 0, sizeof(int), st);
         if (e == cudaSuccess) e = launch_validate(ctx, b, ctx->err_d + 1, st);
