@@ -35,10 +35,12 @@ constexpr int WMAX = 256;      // union window columns per column chunk
 constexpr int LPR = 4;         // lanes per row in the forward GEMM
 constexpr int NPH_MAX = 256;   // phase nodes supported
 constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memory per CTA
+constexpr int ITEM_MAX = 128;  // samples ordered together (a multiple of every tile)
 
 
 struct Lay {
-    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, pm, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, total;
+    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, pm, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, key,
+        perm, total;
     __host__ __device__ Lay(int tj, bool grad, int n_phase) {
         const int wps = tj >= WARPS ? 1 : WARPS / tj;
         const int nslot = tj > WARPS ? tj : WARPS;  // (warp, sample) slots
@@ -65,6 +67,8 @@ struct Lay {
         Yw = o;      o = al16(o + (grad ? 4 * (size_t)nslot * n_phase : 0));
         kst = o;     o = al16(o + 4 * (size_t)WARPS * 128);
         red = o;     o = al16(o + 8 * (size_t)nslot * 8);
+        key = o;     o = al16(o + 8 * ITEM_MAX);
+        perm = o;    o = al16(o + 4 * ITEM_MAX);
         total = o;
     }
 };
@@ -276,6 +280,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     float *sFlux = (float *)(smem + L.flux);
     float *sSig = (float *)(smem + L.sig);  // 1 / fluxerr
     double *sRed = (double *)(smem + L.red);
+    double *sKey = (double *)(smem + L.key);  // [ITEM_MAX] t0 of the item's samples
+    int *sPerm = (int *)(smem + L.perm);      // [ITEM_MAX] samples in t0 order
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int NB = m.bands.n_bands;
@@ -307,12 +313,35 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
         const int64_t ob0 = wi.obs0;
         const int64_t nobs = wi.nobs;
         if (tid == 0) sMisc[2] = 0;  // any invalid observation in this supernova
+
         const bool one_obs_chunk = nobs <= OBS_MAX;
 
         for (int jt = 0; jt < wi.nj; jt += TJ) {
             const int nj = min(TJ, wi.nj - jt);
-            const int64_t pj0 = wi.par0 + jt;  // global index of tile sample 0
-            const int jloc0 = wi.jloc0 + jt;   // local index of tile sample 0
+            // the item's samples are taken in t0 order within groups of ITEM_MAX (ties
+            // by position, non-finite last): a tile's samples then share most of their
+            // phase rows, so the row dots run over smaller row unions; each sample's
+            // outputs still go to its own place
+            const int g0 = jt - jt % ITEM_MAX;  // first sample of this tile's group
+            if (jt == g0) {
+                const int gn = min(ITEM_MAX, wi.nj - g0);
+                __syncthreads();  // the previous group's readers of sPerm are done
+                if (tid < gn) {
+                    const double t = b.t0[wi.par0 + g0 + tid];
+                    sKey[tid] = isfinite(t) ? t : __longlong_as_double(0x7ff0000000000000ll);
+                }
+                __syncthreads();
+                if (tid < gn) {
+                    const double k = sKey[tid];
+                    int r = 0;
+                    for (int i = 0; i < gn; ++i) {
+                        const double ki = sKey[i];
+                        r += (ki < k) || (ki == k && i < tid);
+                    }
+                    sPerm[r] = g0 + tid;
+                }
+            }
+            const int *tperm = sPerm + (jt - g0);  // tile slot -> the sample's position in the item
 
             // ---- per-sample parameters
             __syncthreads();
@@ -322,8 +351,9 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                 double t0 = 0.0;
                 int ok = 0;
                 if (j < nj) {
-                    z = b.z[pj0 + j]; x0 = b.x0[pj0 + j]; x1 = b.x1[pj0 + j]; c = b.c[pj0 + j];
-                    t0 = b.t0[pj0 + j];
+                    const int64_t pj = wi.par0 + tperm[j];
+                    z = b.z[pj]; x0 = b.x0[pj]; x1 = b.x1[pj]; c = b.c[pj];
+                    t0 = b.t0[pj];
                     ok = isfinite(z) && z > -1.f && isfinite(x0) && isfinite(x1) && isfinite(c) &&
                          isfinite(t0);
                     if (!ok) atomicOr(o.err, ERRBIT_PARAM);
@@ -630,7 +660,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     const float2 B = __fmul2_rn(pre, Bs);
                                     if (!isfinite(B.x) || (actb && !isfinite(B.y))) atomicOr(o.err, ERRBIT_RANGE);
                                     if (MODE == MODE_BANDFLUX) {
-                                        float *bo = o.bandflux + wi.bf0 + (int64_t)(jloc0 + j) * nobs + oc;
+                                        float *bo = o.bandflux + wi.bf0 + (int64_t)(wi.jloc0 + tperm[j]) * nobs + oc;
                                         bo[ia] = B.x;
                                         if (actb) bo[ib] = B.y;
                                     } else {
@@ -768,11 +798,12 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         for (int q = 0; q < 6; ++q) g[q] += (float)sRed[w * 8 + 1 + q];
                     }
                     const bool bad = sPj[PJ_OK * TJ + j] == 0.f || sMisc[2] != 0;
-                    o.chi2[pj0 + j] = bad ? __longlong_as_double(0x7ff8000000000000ll) : x2;
+                    const int64_t pj = wi.par0 + tperm[j];
+                    o.chi2[pj] = bad ? __longlong_as_double(0x7ff8000000000000ll) : x2;
                     if (GRAD) {
                         const float gout[5] = {g[0] + g[5], g[1], g[2], g[3], g[4]};
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) o.grad[5 * (pj0 + j) + q] = bad ? qnanf() : gout[q];
+                        for (int q = 0; q < 5; ++q) o.grad[5 * pj + q] = bad ? qnanf() : gout[q];
                     }
                 }
             } else {
@@ -782,7 +813,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     const bool bad = sPj[PJ_OK * TJ + j] == 0.f || sMisc[2] != 0;
                     if (bad)
                         for (int64_t i = tid; i < nobs; i += THREADS)
-                            o.bandflux[wi.bf0 + (int64_t)(jloc0 + j) * nobs + i] = qnanf();
+                            o.bandflux[wi.bf0 + (int64_t)(wi.jloc0 + tperm[j]) * nobs + i] = qnanf();
                 }
             }
         }  // tiles
