@@ -106,6 +106,9 @@ __device__ __forceinline__ void ebuild_point2(const ModelParams &m, float2 lamk,
 // then ends there), and otherwise writes it alone after the main pass. The
 // segmented scan and the column writes then run once per 64 band samples.
 // Columns `estride` apart from e0 (column cc).
+// FULL: the chunk [cc, cc + W) holds every column the band samples touch (a
+// single chunk), so the column checks are left out.
+template <bool FULL = false>
 __device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *lam, const float *wk, int kl,
                                             int k_begin, int stride, float a, float c, int cc, int W, int lane,
                                             float *e0, int estride) {
@@ -167,7 +170,7 @@ __device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *l
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int col = key + q;
-            if (act && tail && col >= cc && col < cc + W) e0[(col - cc) * estride] += v[q];
+            if (act && tail && (FULL || (col >= cc && col < cc + W))) e0[(col - cc) * estride] += v[q];
             __syncwarp();
         }
         // first samples that stand alone (a run of one band sample, or the
@@ -176,7 +179,7 @@ __device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *l
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int col = fa + q;
-                if (alone && col >= cc && col < cc + W) e0[(col - cc) * estride] += va[q];
+                if (alone && (FULL || (col >= cc && col < cc + W))) e0[(col - cc) * estride] += va[q];
                 __syncwarp();
             }
         }
@@ -380,6 +383,7 @@ __device__ __forceinline__ void eadjoint(const ModelParams &m, const float *lam,
 // strided by `stride`, through the packed FP32 instructions on the uniform
 // wavelength axis; each lane adds k's terms, then k + 32's, so with one warp
 // per sample (stride 64) the lane sums are those of eadjoint with stride 32.
+template <bool FULL = false>
 __device__ __forceinline__ void eadjoint_pair(const ModelParams &m, const float *lam, const float *wk, int kl,
                                               int k_begin, int stride, float a, float c, int cc, int W, int lane,
                                               const float *Q, int qstride, float &gc, float &gz) {
@@ -405,7 +409,9 @@ __device__ __forceinline__ void eadjoint_pair(const ModelParams &m, const float 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int ca = fa + q - cc, cb = fb + q - cc;
-            qv[q] = make_float2((ca >= 0 && ca < W) ? Q[ca * qstride] : 0.f, (cb >= 0 && cb < W) ? Q[cb * qstride] : 0.f);
+            qv[q] = FULL ? make_float2(Q[ca * qstride], Q[cb * qstride])
+                         : make_float2((ca >= 0 && ca < W) ? Q[ca * qstride] : 0.f,
+                                       (cb >= 0 && cb < W) ? Q[cb * qstride] : 0.f);
         }
         // Catmull-Rom coefficients (interior) or the straight line (edge interval), per half
         float2 c0 = qv[1];

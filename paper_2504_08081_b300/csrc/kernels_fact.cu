@@ -545,8 +545,12 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                 const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
                                 float *e0 = (WPS == 1) ? sE + j : sEp + warp * WMAX;
-                                ebuild_pair(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, e0,
-                                            (WPS == 1) ? TJ : 1);
+                                if (n_cchunks == 1)
+                                    ebuild_pair<true>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, e0,
+                                                      (WPS == 1) ? TJ : 1);
+                                else
+                                    ebuild_pair<false>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, e0,
+                                                       (WPS == 1) ? TJ : 1);
                             }
                         }
                         __syncthreads();
@@ -761,8 +765,12 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
                                     const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                     const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
-                                    eadjoint_pair(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, sQf + j, TJ,
-                                             gacc[jj][4], gacc[jj][5]);
+                                    if (n_cchunks == 1)
+                                        eadjoint_pair<true>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane,
+                                                            sQf + j, TJ, gacc[jj][4], gacc[jj][5]);
+                                    else
+                                        eadjoint_pair<false>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane,
+                                                             sQf + j, TJ, gacc[jj][4], gacc[jj][5]);
                                 }
                             }
                         }
