@@ -13,14 +13,15 @@
 //   1. builds E (and, for the gradient, E_c = dE/dc and E_z, the lambda' part
 //      of dE/dz) over the tile's union column window,
 //   2. forms the row dots D[r][j] = sum_col G[r][col] E_j[col] for every phase
-//      row an observation touches (a small GEMM on FP32 FMA),
+//      row an observation touches (a small GEMM on packed FP32 FMA),
 //   3. finishes each (observation, sample) pair from 4 row dots: bandflux,
 //      residual, FP64 chi^2 and the direct gradient terms, and scatters the
 //      adjoint weights Y[r][j] += g_ij pre_ij phi_r(p_ij),
 //   4. (gradient) back-projects Q_j[col] = sum_r Y[r][j] (G0 + x1 G1)[r][col]
 //      and dots Q with E_c and E_z for dchi2/dc and the lambda' part of dchi2/dz.
-// Every sum has a fixed order, so results are bitwise reproducible for a
-// given tile size.
+// Tiles take an item's samples in t0 order, so their phase rows mostly
+// coincide. Every sum has a fixed order, so results are bitwise reproducible
+// for a given tile size.
 #include <cstdio>
 
 #include "fact_common.cuh"
@@ -564,12 +565,21 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             }
                             __syncthreads();
                         }
-                        // forward GEMM over the touched rows: LPR lanes per row, 4 columns in flight
+                        // forward GEMM over the touched rows: LPR lanes per row, 8 columns in flight
                         {
                             constexpr int RPW = 32 / LPR;
                             const int l4 = lane % LPR;
-                            for (int rbase = 0; rbase < nrows; rbase += WARPS * RPW) {
-                                const int rr = rbase + warp * RPW + lane / LPR;
+                            // few rows (an 8-sample tile's usual case): two warps per row group,
+                            // each over half the columns, so every warp has work; the first
+                            // half's sums are added to D before the second's (a fixed order)
+                            const bool split = TJ == 8 && nrows <= (WARPS / 2) * RPW;
+                            const int half = split ? warp / (WARPS / 2) : 0;
+                            const int wrow = split ? warp % (WARPS / 2) : warp;
+                            const int Wh = (W + 1) / 2;
+                            const int c0 = split && half ? Wh : 0;
+                            const int c1 = split && !half ? Wh : W;
+                            for (int rbase = 0; rbase < nrows; rbase += (split ? WARPS / 2 : WARPS) * RPW) {
+                                const int rr = rbase + wrow * RPW + lane / LPR;
                                 const bool valid = rr < nrows;
                                 const int r = valid ? sRows[rr] : 0;
                                 float acc0[TJ], acc1[TJ];  // per sample: M0 and M1 row dots
@@ -585,7 +595,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                         a0[p] = make_float2(0.f, 0.f); a1[p] = make_float2(0.f, 0.f);
                                     }
                                     if (valid)
-                                        fwd_row_dot<TJ, false>(m.g01 + (size_t)r * m.nw_pitch + cc, W, l4, sE, a0, a1);
+                                        fwd_row_dot<TJ, false>(m.g01 + (size_t)r * m.nw_pitch + cc + c0, c1 - c0, l4,
+                                                               sE + c0 * TJ, a0, a1);
 #pragma unroll
                                     for (int p = 0; p < TJ / 2; ++p) {
                                         acc0[2 * p] = a0[p].x; acc0[2 * p + 1] = a0[p].y;
@@ -600,14 +611,17 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                         acc1[j] += __shfl_xor_sync(0xffffffffu, acc1[j], sh);
                                     }
                                 }
-                                if (valid && l4 == 0) {
+                                for (int ph = 0; ph < (split ? 2 : 1); ++ph) {
+                                    if (ph == 1) __syncthreads();  // first half's columns added first
+                                    if (valid && l4 == 0 && half == ph) {
 #pragma unroll
-                                    for (int j = 0; j < TJ; ++j) {
-                                        float2 *dv = reinterpret_cast<float2 *>(sD + (j * NP + r) * 2);
-                                        float2 d = *dv;
-                                        d.x += acc0[j];
-                                        d.y += acc1[j];
-                                        *dv = d;
+                                        for (int j = 0; j < TJ; ++j) {
+                                            float2 *dv = reinterpret_cast<float2 *>(sD + (j * NP + r) * 2);
+                                            float2 d = *dv;
+                                            d.x += acc0[j];
+                                            d.y += acc1[j];
+                                            *dv = d;
+                                        }
                                     }
                                 }
                             }
@@ -721,7 +735,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             const int W = min(WMAX, C_hi - cc + 1);
                             __syncthreads();
                             // partial Q per (row subset, column): threads = column + row split
-                            const int Wp = (W + 31) & ~31;
+                            // (W threads per row subset, so nearly all threads have a column)
+                            const int Wp = W;
                             const int nrs = THREADS / Wp;
                             {
                                 const int col = tid % Wp, rs = tid / Wp;
