@@ -711,8 +711,10 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                 if (GRAD) {
                                     y_scatter(yw, yval, lane, fa,
                                               make_float4(coef.x * w[0].x, coef.x * w[1].x, coef.x * w[2].x, coef.x * w[3].x));
-                                    y_scatter(yw, yval, lane, fb,
-                                              make_float4(coef.y * w[0].y, coef.y * w[1].y, coef.y * w[2].y, coef.y * w[3].y));
+                                    if (base + 32 < nb_obs)  // (warp-uniform: some lane has an observation il + 32)
+                                        y_scatter(yw, yval, lane, fb,
+                                                  make_float4(coef.y * w[0].y, coef.y * w[1].y, coef.y * w[2].y,
+                                                              coef.y * w[3].y));
                                 }
                             }
                         }
