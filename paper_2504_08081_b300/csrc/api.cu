@@ -84,6 +84,12 @@ bool band_tables(const salt_band_desc &bd, std::vector<float> &lam, std::vector<
         lam.push_back((float)bd.wave[k]);
         w.push_back((float)(wk[k] / Z));
     }
+    // every band starts on an even index (8-byte aligned), so kernels can read
+    // two consecutive samples with one load; the pad sample has zero weight
+    if (lam.size() & 1) {
+        lam.push_back(lam.back());
+        w.push_back(0.f);
+    }
     return true;
 }
 
@@ -162,17 +168,16 @@ extern "C" int salt_init_model(const salt_model_desc *md, const salt_band_desc *
     // the AB photon integral Z_b (FP64 on the host, then float32)
     std::vector<float> lam_h, w_h;
     mp.bands.n_bands = n_bands;
-    int off = 0;
     for (int b = 0; b < n_bands; ++b) {
         const salt_band_desc &bd = bands[b];
+        const int off = (int)lam_h.size();
         if (!band_tables(bd, lam_h, w_h)) { delete ctx; return SALT_ERR_INVALID; }
         mp.bands.off[b] = off;
         mp.bands.n[b] = bd.n;
         mp.bands.lam_lo[b] = (float)bd.wave[0];
         mp.bands.lam_hi[b] = (float)bd.wave[bd.n - 1];
-        off += bd.n;
     }
-    mp.bands.k_total = off;
+    mp.bands.k_total = (int)lam_h.size();
     // interleaved (M0, M1) rows with an even pitch so every row starts on 16 bytes
     const int nwp = md->n_wave + (md->n_wave & 1);
     mp.nw_pitch = nwp;
@@ -288,11 +293,11 @@ extern "C" int salt_register_band(salt_ctx *ctx, const salt_band_desc *band, int
     ctx->band_w_d = w_d;
     BandTable &bt = ctx->mp.bands;
     const int b = bt.n_bands;
-    bt.off[b] = bt.k_total;
+    bt.off[b] = bt.k_total;  // (even: every band is padded to an even length)
     bt.n[b] = band->n;
     bt.lam_lo[b] = (float)band->wave[0];
     bt.lam_hi[b] = (float)band->wave[band->n - 1];
-    bt.k_total += band->n;
+    bt.k_total = (int)lam.size();
     bt.n_bands = b + 1;
     ctx->mp.band_lam = lam_d;
     ctx->mp.band_w = w_d;

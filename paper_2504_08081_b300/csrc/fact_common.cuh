@@ -100,46 +100,51 @@ __device__ __forceinline__ void ebuild_point2(const ModelParams &m, float2 lamk,
 
 // The column-response build of ebuild with two consecutive band samples per
 // lane (k = k0 + 2 lane and k0 + 2 lane + 1, chunks of 64 strided by
-// `stride`): a lane whose two samples share their first tap column adds them
-// locally; a lane whose pair straddles two columns hands its first sample to
-// the previous lane when that lane's run has the same first column (the run
-// then ends there), and otherwise writes it alone after the main pass. The
-// segmented scan and the column writes then run once per 64 band samples.
-// Columns `estride` apart from e0 (column cc).
+// `stride`, k0 even, so each lane reads its two band samples with one 8-byte
+// load: every band starts on an even index of the padded tables; samples below
+// k_lo or above kl are inactive): a lane whose two samples share their first
+// tap column adds them locally; a lane whose pair straddles two columns hands
+// its first sample to the previous lane when that lane's run has the same
+// first column (the run then ends there), and otherwise writes it alone after
+// the main pass. The segmented scan and the column writes then run once per 64
+// band samples. Columns `estride` apart from e0 (column cc).
 // FULL: the chunk [cc, cc + W) holds every column the band samples touch (a
 // single chunk), so the column checks are left out.
 template <bool FULL = false>
-__device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *lam, const float *wk, int kl,
+__device__ __forceinline__ void ebuild_pair(const ModelParams &m, const float *lam, const float *wk, int k_lo, int kl,
                                             int k_begin, int stride, float a, float c, int cc, int W, int lane,
                                             float *e0, int estride) {
     for (int k0 = k_begin; k0 <= kl; k0 += stride) {
         const int ka = k0 + 2 * lane, kb = ka + 1;
-        const bool acta = ka <= kl, actb = kb <= kl;
+        const bool acta = ka >= k_lo && ka <= kl, actb = kb >= k_lo && kb <= kl;
         int fa = 0x40000000 + 2 * lane, fb = fa + 1;  // inactive: keys of their own, never written
         float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
         if (m.wnode) {  // node axis: binary searches, one band sample at a time
             if (acta) ebuild_point(m, lam, wk, ka, a, c, fa, va);
             if (actb) ebuild_point(m, lam, wk, kb, a, c, fb, vb);
-        } else if (acta) {
-            const int kb2 = actb ? kb : ka;
+        } else if (acta || actb) {
+            // (ka, ka + 1) lie inside the band's padded run of samples
+            const float2 l2 = *reinterpret_cast<const float2 *>(lam + ka);
+            const float2 w2 = *reinterpret_cast<const float2 *>(wk + ka);
             int f0, f1;
             float2 v2[4];
-            ebuild_point2(m, make_float2(lam[ka], lam[kb2]), make_float2(wk[ka], wk[kb2]), a, kColour * c, f0, f1,
-                          v2);
-            fa = f0;
+            ebuild_point2(m, l2, w2, a, kColour * c, f0, f1, v2);
+            if (acta) {
+                fa = f0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) va[q] = v2[q].x;
+                for (int q = 0; q < 4; ++q) va[q] = v2[q].x;
+            }
             if (actb) {
                 fb = f1;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) vb[q] = v2[q].y;
             }
         }
-        const bool split = actb && fa != fb;  // (then acta as well)
+        const bool split = acta && actb && fa != fb;
         const int key = actb ? fb : fa;
         float v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (actb && !split) ? va[q] + vb[q] : (actb ? vb[q] : va[q]);
+        for (int q = 0; q < 4; ++q) v[q] = (acta && actb && !split) ? va[q] + vb[q] : (actb ? vb[q] : va[q]);
         // a straddling pair's first sample joins the previous lane's run when
         // that run has its first column
         const int prevkey = __shfl_up_sync(0xffffffffu, key, 1);

@@ -37,13 +37,17 @@ constexpr int LPR = 4;         // lanes per row in the forward GEMM
 constexpr int NPH_MAX = 256;   // phase nodes supported
 constexpr int KTOT = 2048;     // band samples (all bands) staged in shared memory per CTA
 constexpr int ITEM_MAX = 128;  // samples ordered together (a multiple of every tile)
+// Row stride of the sample-major column arrays (the build's staging rows, Q):
+// WMAX + 4 columns, 4 modulo 32 banks, so that a warp reading 4 consecutive
+// columns of 8 samples, or 32 consecutive columns of one sample, touches 32
+// distinct banks.
+constexpr int ES = WMAX + 4;
 
 
 struct Lay {
-    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, pm, rowmask, rows, misc, E, Ep, Q, D, Yw, kst, red, key,
+    size_t ord, zpf, band, mjd, flux, sig, bst, lam, wk, pj, pm, rowmask, rows, misc, E, Q, D, Yw, kst, red, key,
         perm, total;
     __host__ __device__ Lay(int tj, bool grad, int n_phase) {
-        const int wps = tj >= WARPS ? 1 : WARPS / tj;
         const int nslot = tj > WARPS ? tj : WARPS;  // (warp, sample) slots
         const bool stage = tj <= 8;                 // 16-sample tiles read band samples through L1
         size_t o = 0;
@@ -61,9 +65,11 @@ struct Lay {
         rowmask = o; o = al16(o + 4 * (NPH_MAX / 32));
         rows = o;    o = al16(o + 4 * NPH_MAX);
         misc = o;    o = al16(o + 4 * 16);
-        E = o;       o = al16(o + 4 * (size_t)WMAX * tj);
-        Ep = o;      o = al16(o + (wps > 1 ? 4 * (size_t)WARPS * WMAX : 0));
-        Q = o;       o = al16(o + (grad ? 4 * (size_t)THREADS * tj : 0));
+        E = o;       o = al16(o + 4 * (size_t)ES * tj);
+        // the column-response staging rows [slot][ES] share their space with the
+        // reverse GEMM partials (never live at the same time)
+        const size_t nq = grad ? (size_t)THREADS * tj : 0, nst = (size_t)nslot * ES;
+        Q = o;       o = al16(o + 4 * (nq > nst ? nq : nst));
         D = o;       o = al16(o + 4 * (size_t)n_phase * tj * 2);
         Yw = o;      o = al16(o + (grad ? 4 * (size_t)nslot * n_phase : 0));
         kst = o;     o = al16(o + 4 * (size_t)WARPS * 128);
@@ -97,7 +103,8 @@ __device__ __forceinline__ void fwd_row_dot(const float2 *grow, int W, int l4, c
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int col = min(col0 + u * LPR, W - 1);
+            const int col = col0 + u * LPR;
+            if (col >= W) break;  // the last pass's slots past the window (all lanes but a column's worth)
             const float2 gx = make_float2(gv[u].x, gv[u].x), gy = make_float2(gv[u].y, gv[u].y);
             if (TJ % 4 == 0) {
                 const float4 *ev = reinterpret_cast<const float4 *>(sE + col * TJ);
@@ -271,9 +278,9 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
     unsigned *sRowMask = (unsigned *)(smem + L.rowmask);
     int *sRows = (int *)(smem + L.rows);
     int *sMisc = (int *)(smem + L.misc);
-    float *sE = (float *)(smem + L.E);     // [WMAX][TJ] column responses (then Q)
-    float *sEp = (float *)(smem + L.Ep);   // [WARPS][WMAX] per-warp partials (WPS > 1)
-    float *sQ = (float *)(smem + L.Q);     // [THREADS][TJ] reverse-GEMM partials, then Q[col][j]
+    float *sE = (float *)(smem + L.E);     // [WMAX][TJ] column responses (then Q as [TJ][ES])
+    float *sSt = (float *)(smem + L.Q);    // [slot][ES] column-response staging rows, one per (warp, sample)
+    float *sQ = (float *)(smem + L.Q);     // [TJ/2][THREADS] float2 reverse-GEMM partials (after the build)
     float *sD = (float *)(smem + L.D);     // [n_phase][TJ][2]
     float *sYw = (float *)(smem + L.Yw);   // [slots][n_phase] adjoint rows per (warp, sample)
     float2 *sMjd = (float2 *)(smem + L.mjd);  // observation times as float pairs
@@ -458,7 +465,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                     if (GRAD)
                         for (int q = tid; q < WARPS * SPW * NP; q += THREADS) sYw[q] = 0.f;
                     __syncthreads();
-                    if (warp == 0 && lane < nj) {
+                    // the window on the last warp: the row marking below starts at warp 0
+                    if (warp == WARPS - 1 && lane < nj) {
                         const int j = lane;
                         const float a = sPj[PJ_A * TJ + j];
                         int kf = K, kl = -1;
@@ -534,37 +542,36 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         const int cc = C_lo + ch * WMAX;
                         const int W = min(WMAX, C_hi - cc + 1);
                         __syncthreads();
-                        for (int q = tid; q < W * TJ; q += THREADS) sE[q] = 0.f;
-                        if (WPS > 1)
-                            for (int q = tid; q < WARPS * WMAX; q += THREADS) sEp[q] = 0.f;
-                        __syncthreads();
+                        // each (warp, sample) slot builds into its own staging row, column
+                        // after column (consecutive banks for the runs' column adds), then
+                        // the rows are summed over a sample's warps in order and transposed
+                        // to E[col][j]
 #pragma unroll
                         for (int jj = 0; jj < SPW; ++jj) {
                             const int j = (warp / WPS) * SPW + jj, sub = warp % WPS;
+                            float *e0 = sSt + (warp * SPW + jj) * ES;
+                            for (int q = lane; q < W; q += 32) e0[q] = 0.f;
+                            __syncwarp();
                             if (j < nj && sPj[PJ_OK * TJ + j] != 0.f) {
                                 const int kf = __float_as_int(sPj[PJ_KF * TJ + j]);
                                 const int kl = __float_as_int(sPj[PJ_KL * TJ + j]);
                                 const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
-                                float *e0 = (WPS == 1) ? sE + j : sEp + warp * WMAX;
+                                const int k0 = (kf & ~1) + 64 * sub;  // even: one 8-byte load per lane's pair
                                 if (n_cchunks == 1)
-                                    ebuild_pair<true>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, e0,
-                                                      (WPS == 1) ? TJ : 1);
+                                    ebuild_pair<true>(m, lam, wk, kf, kl, k0, 64 * WPS, a, c, cc, W, lane, e0, 1);
                                 else
-                                    ebuild_pair<false>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane, e0,
-                                                       (WPS == 1) ? TJ : 1);
+                                    ebuild_pair<false>(m, lam, wk, kf, kl, k0, 64 * WPS, a, c, cc, W, lane, e0, 1);
                             }
                         }
                         __syncthreads();
-                        if (WPS > 1) {
-                            for (int q = tid; q < W * TJ; q += THREADS) {
-                                const int col = q / TJ, j = q - col * TJ;
-                                float acc = 0.f;
+                        for (int q = tid; q < W * TJ; q += THREADS) {
+                            const int col = q / TJ, j = q - col * TJ;
+                            float acc = 0.f;
 #pragma unroll
-                                for (int sb = 0; sb < WPS; ++sb) acc += sEp[(j * WPS + sb) * WMAX + col];
-                                sE[col * TJ + j] = acc;
-                            }
-                            __syncthreads();
+                            for (int sb = 0; sb < WPS; ++sb) acc += sSt[(j * WPS + sb) * ES + col];
+                            sE[col * TJ + j] = acc;
                         }
+                        __syncthreads();
                         // forward GEMM over the touched rows: LPR lanes per row, 8 columns in flight
                         {
                             constexpr int RPW = 32 / LPR;
@@ -738,8 +745,12 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             __syncthreads();
                             // partial Q per (row subset, column): threads = column + row split
                             // (W threads per row subset, so nearly all threads have a column)
+                            // row subsets: the fewest that keep the fewest passes of the
+                            // 8-row unrolled loop (fewer busy warps, the same latency)
                             const int Wp = W;
-                            const int nrs = THREADS / Wp;
+                            const int nrs_max = THREADS / Wp;
+                            const int passes = max(1, ((nrows + nrs_max - 1) / nrs_max + 7) / 8);
+                            const int nrs = max(1, min(nrs_max, (nrows + 8 * passes - 1) / (8 * passes)));
                             {
                                 const int col = tid % Wp, rs = tid / Wp;
                                 if constexpr (TJ == 1) {
@@ -758,19 +769,36 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                         rev_col_dot<TJ, false>(m.g01 + cc + col, (size_t)m.nw_pitch, sRows, rs, nrs,
                                                                nrows, sY, q0, q1);
                                     const float2 *x1p = reinterpret_cast<const float2 *>(sPj + PJ_X1 * TJ);
-                                    float2 *qo = reinterpret_cast<float2 *>(sQ + tid * TJ);
+                                    float2 *qo = reinterpret_cast<float2 *>(sQ) + tid;
 #pragma unroll
-                                    for (int p = 0; p < TJ / 2; ++p) qo[p] = __ffma2_rn(x1p[p], q1[p], q0[p]);
+                                    for (int p = 0; p < TJ / 2; ++p) qo[p * THREADS] = __ffma2_rn(x1p[p], q1[p], q0[p]);
                                 }
                             }
                             __syncthreads();
-                            // Q[col][j] = sum over row subsets in order (into the E buffer, free now)
+                            // Q_j[col] = sum over row subsets in order, sample-major with row
+                            // stride ES (into the E buffer, free now): warps take sample pairs,
+                            // lanes consecutive columns
                             float *sQf = sE;
-                            for (int q = tid; q < W * TJ; q += THREADS) {
-                                const int col = q / TJ, j = q - col * TJ;
-                                float qv = 0.f;
-                                for (int rs = 0; rs < nrs; ++rs) qv += sQ[(rs * Wp + col) * TJ + j];
-                                sQf[col * TJ + j] = qv;
+                            if constexpr (TJ == 1) {
+                                for (int col = tid; col < W; col += THREADS) {
+                                    float qv = 0.f;
+                                    for (int rs = 0; rs < nrs; ++rs) qv += sQ[rs * Wp + col];
+                                    sQf[col] = qv;
+                                }
+                            } else {
+                                constexpr int NPAIR = TJ / 2, WPP = WARPS / NPAIR;  // warps per sample pair
+                                const float2 *qp = reinterpret_cast<const float2 *>(sQ) + (warp / WPP) * THREADS;
+                                float *q0 = sQf + (2 * (warp / WPP)) * ES;
+                                for (int col = (warp % WPP) * 32 + lane; col < W; col += 32 * WPP) {
+                                    float2 qv = make_float2(0.f, 0.f);
+                                    for (int rs = 0; rs < nrs; ++rs) {
+                                        const float2 v = qp[rs * Wp + col];
+                                        qv.x += v.x;
+                                        qv.y += v.y;
+                                    }
+                                    q0[col] = qv.x;
+                                    q0[ES + col] = qv.y;
+                                }
                             }
                             __syncthreads();
                             // adjoint of the column response per band sample: dchi2/dc and the
@@ -784,10 +812,10 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     const float a = sPj[PJ_A * TJ + j], c = sPj[PJ_C * TJ + j];
                                     if (n_cchunks == 1)
                                         eadjoint_pair<true>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane,
-                                                            sQf + j, TJ, gacc[jj][4], gacc[jj][5]);
+                                                            sQf + j * ES, 1, gacc[jj][4], gacc[jj][5]);
                                     else
                                         eadjoint_pair<false>(m, lam, wk, kl, kf + 64 * sub, 64 * WPS, a, c, cc, W, lane,
-                                                             sQf + j, TJ, gacc[jj][4], gacc[jj][5]);
+                                                             sQf + j * ES, 1, gacc[jj][4], gacc[jj][5]);
                                 }
                             }
                         }

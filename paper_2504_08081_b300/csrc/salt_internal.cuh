@@ -28,8 +28,8 @@ enum : int { ERRBIT_BAND = 1, ERRBIT_SIGMA = 2, ERRBIT_PARAM = 4, ERRBIT_RANGE =
 // Band table passed by value to every kernel (fits the kernel parameter space).
 struct BandTable {
     int n_bands;
-    int k_total;  // band samples over all bands (flat arrays)
-    int off[SALT_MAX_BANDS];  // first sample of band b in the flat arrays
+    int k_total;  // length of the flat arrays: every band's samples, each band padded to an even length
+    int off[SALT_MAX_BANDS];  // first sample of band b in the flat arrays (even)
     int n[SALT_MAX_BANDS];    // samples in band b
     float lam_lo[SALT_MAX_BANDS], lam_hi[SALT_MAX_BANDS];  // first / last observer wavelength
 };
