@@ -403,11 +403,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         atomicOr(o.err, okb ? ERRBIT_SIGMA : ERRBIT_BAND);
                         sMisc[2] = 1;
                     }
-                    sZpf[i] = zp_scale(b.zp[obase + i]);
                     sBand[i] = (okb && e > 0.f) ? bd : -1;
-                    sMjd[i] = split_f2(b.mjd[obase + i]);
-                    sFlux[i] = b.flux[obase + i];
-                    sSig[i] = 1.0f / e;  // 1/sigma (never used when e <= 0: band id -1)
                 }
                 __syncthreads();
                 if (warp == 0) {
@@ -441,11 +437,26 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         }
                         const unsigned mm = __match_any_sync(0xffffffffu, bd);
                         const int rank = __popc(mm & ((1u << lane) - 1u));
-                        if (bd >= 0) sOrd[pos[bd] + rank] = i;
+                        if (bd >= 0) {
+                            const int ps = pos[bd] + rank;
+                            sOrd[ps] = i;
+                            sBand[i] = ps;  // from here on: the observation's sorted position
+                        }
                         __syncwarp();
                         if (bd >= 0 && lane == __ffs(mm) - 1) pos[bd] += __popc(mm);
                         __syncwarp();
                     }
+                }
+                __syncthreads();
+                // the valid observations' values staged in band-sorted order: a band's
+                // observations are then consecutive (conflict-free reads in the epilogue)
+                for (int i = tid; i < nc; i += THREADS) {
+                    const int ps = sBand[i];
+                    if (ps < 0) continue;
+                    sZpf[ps] = zp_scale(b.zp[obase + i]);
+                    sMjd[ps] = split_f2(b.mjd[obase + i]);
+                    sFlux[ps] = b.flux[obase + i];
+                    sSig[ps] = 1.0f / b.fluxerr[obase + i];
                 }
                 __syncthreads();
                 }
@@ -453,7 +464,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                 for (int bd = 0; bd < NB; ++bd) {
                     const int nb_obs = sBst[bd + 1] - sBst[bd];
                     if (nb_obs == 0) continue;  // uniform: sBst is shared
-                    const int *ordb = sOrd + sBst[bd];
+                    const int ob0s = sBst[bd];  // the band's first observation in sorted order
                     const int K = m.bands.n[bd], koff = m.bands.off[bd];
                     const float *lam = (bands_staged ? sLam : m.band_lam) + koff;
                     const float *wk = (bands_staged ? sWk : m.band_w) + koff;
@@ -500,7 +511,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                         if (q < nb_obs * nj) {
                             const int il = q / nj, j = q - il * nj;
                             if (sPj[PJ_OK * TJ + j] != 0.f) {
-                                const int i = ordb[il];
+                                const int i = ob0s + il;
                                 int iv; float t, iwp, p;
                                 if (phase_find(m, sMjd[i], sPm[j], iv, t, iwp, p))
                                     first = first_tap(iv, NP);
@@ -651,7 +662,7 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                             for (int base = sub * 64; base < nb_obs; base += 64 * WPS) {
                                 const int ila = base + lane, ilb = ila + 32;
                                 const bool acta = ila < nb_obs, actb = ilb < nb_obs;
-                                const int ia = ordb[acta ? ila : 0], ib = ordb[actb ? ilb : 0];
+                                const int ia = ob0s + (acta ? ila : 0), ib = ob0s + (actb ? ilb : 0);
                                 bool oka = false, okb = false;
                                 int iva = 0, ivb = 0;
                                 float2 t = f2(0.f), iwp = f2(0.f), p = f2(0.f);
@@ -686,8 +697,8 @@ k_fact(ModelParams m, BatchDev b, OutDev o, const WorkItem *__restrict__ items, 
                                     if (!isfinite(B.x) || (actb && !isfinite(B.y))) atomicOr(o.err, ERRBIT_RANGE);
                                     if (MODE == MODE_BANDFLUX) {
                                         float *bo = o.bandflux + wi.bf0 + (int64_t)(wi.jloc0 + tperm[j]) * nobs + oc;
-                                        bo[ia] = B.x;
-                                        if (actb) bo[ib] = B.y;
+                                        bo[sOrd[ia]] = B.x;
+                                        if (actb) bo[sOrd[ib]] = B.y;
                                     } else {
                                         const float2 isig = make_float2(sSig[ia], sSig[ib]);
                                         const float2 r = __fmul2_rn(fsub2(make_float2(sFlux[ia], sFlux[ib]), B), isig);
